@@ -1,0 +1,402 @@
+#!/usr/bin/env python3
+"""Benchmark: depth points fused per second (allocate + integrate) on one
+640x480 synthetic room frame into a hash-blocked TSDF volume (voxel 5 mm,
+truncation 2 cm, 2^20 table slots, 2^18 pool blocks).
+
+One step = one pass of the whole hot path (stage A allocate + stage B
+integrate, paper Section 2.2) over one frame, into a freshly reset volume (so
+stage A never degenerates into a lookup-only pass, Section 4.2). Between steps,
+outside the timed events, the volume is reset and L2 is flushed by a 512 MB
+write. Each step is timed with CUDA events on the launching stream; stage A
+and stage B also have their own events.
+
+Prints ONE JSON line. With --impl reference the CPU oracle (single thread,
+host cores) is timed on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("depth pts fused/s (alloc+integrate, 640x480) + % HBM roofline; "
+          "serving p50/p99")
+UNIT = "pts/s"
+WORKLOAD = "room_640x480_single_frame"
+N_FRAMES = 4           # distinct orbit frames, cycled over the steps
+FLUSH_BYTES = 512 << 20
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def config_dict(spec, frames):
+    return {"workload": WORKLOAD, "width": 640, "height": 480,
+            "voxel_m": spec.voxel_size, "truncation_m": spec.truncation,
+            "table_slots": spec.table_slots, "pool_blocks": spec.pool_blocks,
+            "points_per_frame": int(np.mean([f.valid_points for f in frames])),
+            "distinct_frames": len(frames), "colour": True,
+            "l2": "flushed between steps (512 MB write outside the timed events)",
+            "volume": "reset between steps: every step fuses into an empty volume"}
+
+
+def make_frames(rank=0):
+    from paper_2608_08287_gb300 import synth
+    return [synth.room_frame(37 * (rank * N_FRAMES + i)) for i in range(N_FRAMES)]
+
+
+# ----------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.rows = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 8:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4)
+                          if r[4 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+# ----------------------------------------------------------------------------
+# traffic from a committed ncu summary, valid only for the current kernel source
+# ----------------------------------------------------------------------------
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("tsdf_device.cuh", "tsdf_kernels.cu"):
+        with open(os.path.join(ROOT, "paper_2608_08287_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(kernel):
+    """dram bytes per launch recorded under profiles/ for this kernel source, else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    src = kernel_source_hash()
+    for line in open(path):
+        parts = line.split()
+        if len(parts) >= 3 and not line.startswith("#") and parts[0] == kernel \
+                and parts[1] == src:
+            return float(parts[2])
+    return None
+
+
+# ----------------------------------------------------------------------------
+# the GPU arm
+# ----------------------------------------------------------------------------
+def run_gpu(args, rank, world, local_rank):
+    import torch
+    from paper_2608_08287_gb300 import synth, tsdf
+    from paper_2608_08287_gb300.build import build_library
+
+    torch.cuda.set_device(local_rank)
+    if rank == 0:
+        build_library()
+    if world > 1:
+        torch.distributed.barrier()
+    spec = synth.ROOM_640
+    frames = make_frames(rank)
+    vol = tsdf.Volume(spec.voxel_size, spec.truncation, spec.table_slots, spec.pool_blocks)
+    for k, x in (("probe_load", args.probe_load), ("integrate_mode", args.integrate_mode)):
+        if x is not None:
+            assert vol.set_option(k, x) == "OK"
+    stream = torch.cuda.Stream()
+    sp = stream.cuda_stream
+    dev = [(torch.from_numpy(f.depth).cuda(), torch.from_numpy(f.rgb).cuda()) for f in frames]
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    W, H = 640, 480
+
+    # per-frame work counts from the GPU result itself (fresh volume each time)
+    work = []
+    for f, (d, c) in zip(frames, dev):
+        assert vol.reset(sp) == "OK"
+        assert tsdf.tsdf_fuse_frame(vol.handle, d, W, H, f.intr, f.pose, c, sp) == "OK"
+        coords, vox = vol.export(sp)
+        work.append({"points": f.valid_points, "blocks": len(coords),
+                     "voxels": int((vox[:, 1] > 0).sum())})
+
+    def one_step(i, evs=None):
+        f = frames[i % len(frames)]
+        d, c = dev[i % len(frames)]
+        vol.reset(sp)
+        with torch.cuda.stream(stream):
+            flush.fill_(i & 0xFF)
+        if evs:
+            evs[0].record(stream)
+        assert tsdf.tsdf_allocate_async(vol.handle, d, W, H, f.intr, f.pose, sp) == "OK"
+        if evs:
+            evs[1].record(stream)
+        assert tsdf.tsdf_integrate_async(vol.handle, d, W, H, f.intr, f.pose, c, sp) == "OK"
+        if evs:
+            evs[2].record(stream)
+        return f.valid_points
+
+    for i in range(args.warmup):
+        one_step(i)
+    assert vol.status(sp) == "OK"
+    torch.cuda.synchronize()
+
+    events = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    launches0 = tsdf.tsdf_launch_count()
+    points = 0
+    with ClockSampler(local_rank) as clk:
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            points += one_step(args.warmup + i, events[i])
+        stream.synchronize()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    if world > 1:
+        torch.distributed.barrier()
+    launches = tsdf.tsdf_launch_count() - launches0
+    st = vol.status(sp)
+    assert st == "OK", st
+    ta = [events[i][0].elapsed_time(events[i][1]) for i in range(args.steps)]
+    tb_ = [events[i][1].elapsed_time(events[i][2]) for i in range(args.steps)]
+    step_ms = [a + b for a, b in zip(ta, tb_)]
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+        pts = torch.tensor([points], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(pts)
+        points_all = int(pts.item())
+    else:
+        points_all = points
+    value = points_all / (total_ms / 1e3)
+
+    # roofline of the dominant stage (Section 8(d) algorithmic bytes)
+    hbm, peak_kind = peaks()
+    mean = lambda k: float(np.mean([w[k] for w in work]))
+    a_bytes = 4 * W * H + 16 * mean("blocks") + 28 * mean("blocks")
+    b_bytes = 7 * W * H + 16 * mean("blocks") + 40 * mean("voxels")
+    a_ms, b_ms = float(np.mean(ta)), float(np.mean(tb_))
+    a_gbs, b_gbs = a_bytes / (a_ms * 1e6), b_bytes / (b_ms * 1e6)
+    dom = ("integrate", b_bytes, b_ms, b_gbs) if b_ms >= a_ms else ("allocate", a_bytes, a_ms, a_gbs)
+    kname = {"integrate": "integrate_kernel", "allocate": "allocate_kernel"}[dom[0]]
+    roof = {"bound": "hbm", "kernel": dom[0], "achieved": round(dom[3], 1), "peak": hbm,
+            "peak_kind": f"{peak_kind} hbm_gbs", "unit": "GB/s",
+            "frac": round(dom[3] / hbm, 4), "algorithmic_bytes": int(dom[1]),
+            "traffic": committed_traffic(kname)}
+
+    # end to end through the public C ABI with host buffers
+    e2e = run_e2e(args, vol, frames, torch, tsdf, sp, stream, flush)
+
+    out = None
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(total_ms / args.steps, 5), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config_dict(spec, frames),
+            "stages": {"allocate_ms": round(a_ms, 5), "integrate_ms": round(b_ms, 5),
+                       "allocate_hbm_frac": round(a_gbs / hbm, 4),
+                       "integrate_hbm_frac": round(b_gbs / hbm, 4),
+                       "step_ms_p50": round(float(np.percentile(step_ms, 50)), 5),
+                       "step_ms_p95": round(float(np.percentile(step_ms, 95)), 5),
+                       "step_ms_p99": round(float(np.percentile(step_ms, 99)), 5),
+                       "blocks_per_frame": mean("blocks"), "voxels_per_frame": mean("voxels")},
+            "roofline": roof,
+            "e2e": e2e,
+            "gpu_launches": int(launches),
+            "gpu_launches_detail": "per step: 1 stage-A + 1 stage-B kernel (timed) + 1 reset "
+                                   "kernel (between steps, outside the step events)",
+            "clocks": clk.summary(),
+            "wall_s_timed_region": round(wall, 4),
+            "kernel_source": kernel_source_hash(),
+        }
+        if not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    return out
+
+
+def run_e2e(args, vol, frames, torch, tsdf, sp, stream, flush):
+    """Same metric through tsdf_fuse_frame_host: pinned host depth + colour are
+    copied in, both stages run, the status word is read back, every step."""
+    host = [(torch.from_numpy(f.depth).pin_memory(), torch.from_numpy(f.rgb).pin_memory())
+            for f in frames]
+    W, H = 640, 480
+    for i in range(max(1, args.warmup)):
+        f = frames[i % len(frames)]
+        vol.reset(sp)
+        assert tsdf.tsdf_fuse_frame_host(vol.handle, host[i % len(frames)][0], W, H, f.intr,
+                                         f.pose, host[i % len(frames)][1], sp) == "OK"
+    total = 0.0
+    points = 0
+    for i in range(args.steps):
+        f = frames[i % len(frames)]
+        d, c = host[i % len(frames)]
+        vol.reset(sp)
+        with torch.cuda.stream(stream):
+            flush.fill_(i & 0xFF)
+        stream.synchronize()
+        t0 = time.perf_counter()
+        st = tsdf.tsdf_fuse_frame_host(vol.handle, d, W, H, f.intr, f.pose, c, sp)
+        total += time.perf_counter() - t0
+        assert st == "OK", st
+        points += f.valid_points
+    return {"value": round(points / total, 1), "unit": UNIT,
+            "h2d_bytes_per_step": W * H * 4 + W * H * 3, "d2h_bytes_per_step": 8,
+            "call": "tsdf_fuse_frame_host (pinned host depth+rgb in, status word out)"}
+
+
+def cpu_baseline(seconds):
+    """The oracle as it stands, single-threaded on a host core, on whole frames."""
+    import oracle
+    from paper_2608_08287_gb300 import synth
+    spec = synth.ROOM_640
+    frames = make_frames(0)[:2]
+    n = 0
+    points = 0
+    t0 = time.perf_counter()
+    while True:
+        f = frames[n % len(frames)]
+        ov = oracle.OracleVolume(spec.voxel_size, spec.truncation, spec.table_slots,
+                                 spec.pool_blocks)
+        assert ov.fuse_frame(f) == "OK"
+        ov.close()
+        n += 1
+        points += f.valid_points
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return {"value": round(points / el, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} whole 640x480 room frames into empty volumes, one thread"}
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle timed on the same workload and metric."""
+    import oracle
+    from paper_2608_08287_gb300 import synth
+    oracle.build()
+    spec = synth.ROOM_640
+    frames = make_frames(0)[:2]
+
+    def step(i):
+        f = frames[i % len(frames)]
+        ov = oracle.OracleVolume(spec.voxel_size, spec.truncation, spec.table_slots,
+                                 spec.pool_blocks)
+        assert ov.fuse_frame(f) == "OK"
+        ov.close()
+        return f.valid_points
+
+    for i in range(args.warmup):
+        step(i)
+    t0 = time.perf_counter()
+    points = sum(step(args.warmup + i) for i in range(args.steps))
+    el = time.perf_counter() - t0
+    value = points / el
+    return {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(el / args.steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "impl": "reference", "config": config_dict(spec, frames),
+            "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": 1,
+                             "kind": "oracle",
+                             "sample": f"{args.steps} whole 640x480 room frames, one thread"},
+            "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--probe-load", type=int, default=None)
+    ap.add_argument("--integrate-mode", type=int, default=None)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)), flush=True)
+        return
+
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    out = run_gpu(args, rank, world, local_rank)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,248 @@
+/*
+ * tsdf.h -- C ABI of libtsdf, hash-blocked TSDF fusion on GB300 (sm_103a).
+ *
+ * The operation is the paper's integration of one depth frame into a
+ * hash-blocked TSDF volume (Section 2, "The workload"):
+ *   stage A, allocate (Section 2.2 "Allocate", Listing 1 in Section 2.3): every
+ *     valid depth point walks its truncation band along its view ray, maps each
+ *     voxel that passes the occlusion test to its 8^3 block, and makes sure the
+ *     block exists in an open-addressed, linearly probed hash table of 16-byte
+ *     entries (64-bit packed key + 32-bit block index, Section 2.1), claiming a
+ *     slot with a 64-bit compare-exchange and a pool index with a counter;
+ *   stage B, update (Section 2.2 "Update"): the same walk and test, a table
+ *     lookup, and weighted SUMS added to five parallel float arrays of the block
+ *     pool (signed distance, weight, red, green, blue; Section 2.1).
+ * Means are recovered on read-out (Section 2.2), here by tsdf_export_blocks.
+ *
+ * Geometry (fixed where the paper is silent; identical in every entry point):
+ *   pixel (u, v) is a pixel centre; its camera ray is ((u-cx)/fx, (v-cy)/fy, 1);
+ *   the band holds 2M+1 samples at range offsets (k-M)*voxel_size, k = 0..2M,
+ *   M = lrintf(truncation / voxel_size), along the unit ray; each distinct voxel
+ *   is taken once per point; a voxel is accepted when its centre is in front of
+ *   the camera, projects (nearest pixel) inside the image onto a valid depth d',
+ *   and lies no more than `truncation` behind it; the stored value is
+ *   clamp((d - z_centre) / truncation, -1, 1), evaluated at the voxel centre
+ *   (Section 4.1); weight 1 per contribution. All integer decisions are taken in
+ *   IEEE single precision with a fixed operation order, so they are reproducible.
+ *
+ * Memory: one device allocation per volume, laid out as
+ *   header (block counter, error word) | table (table_slots x 16 B) |
+ *   block coordinates (pool_blocks x 3 int32) |
+ *   5 channel arrays (pool_blocks x 512 float32 each).
+ * A block with pool index i owns floats [i*512, (i+1)*512) of each channel; the
+ * voxel (lx, ly, lz) of a block is local index lx + 8*ly + 64*lz.
+ * Block coordinates are floor(voxel / 8) and must lie in [-2^20, 2^20); the
+ * packed key is (bx+2^20)<<42 | (by+2^20)<<21 | (bz+2^20) (Section 2.1).
+ *
+ * Streams: every `stream` argument is a cudaStream_t passed as void*
+ * (NULL = the legacy default stream). Device pointers must be on the device
+ * that was current when the volume was created, and that device must be
+ * current when the volume is used.
+ *
+ * Errors: every call returns a status; nothing throws across the ABI. Table or
+ * pool overflow is never silent: the fusion call reports it and the volume is
+ * POISONED (later fusion calls return TSDF_ERR_POISONED and do nothing) until
+ * tsdf_volume_reset. The probe is unbounded in the paper's sense (it scans
+ * until it finds the key or an empty slot); a scan of the whole table reports
+ * TSDF_ERR_TABLE_FULL instead of looping.
+ */
+#ifndef TSDF_H_
+#define TSDF_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tsdf_volume tsdf_volume; /* opaque, owned by the library */
+
+typedef enum tsdf_status {
+  TSDF_OK = 0,
+  TSDF_ERR_INVALID_ARG = 1,      /* bad argument; nothing was enqueued */
+  TSDF_ERR_OUT_OF_MEMORY = 2,    /* a device or pinned allocation failed */
+  TSDF_ERR_POOL_FULL = 3,        /* more blocks than pool_blocks (Section 3.4) */
+  TSDF_ERR_TABLE_FULL = 4,       /* a probe scanned every slot without room */
+  TSDF_ERR_PUBLISH_TIMEOUT = 5,  /* a waiter gave up on an unpublished index */
+  TSDF_ERR_BOUNDS = 6,           /* an index check failed (defensive) */
+  TSDF_ERR_POISONED = 7,         /* volume holds an earlier error; reset it */
+  TSDF_ERR_CUDA = 8              /* a CUDA runtime call failed */
+} tsdf_status;
+
+typedef struct tsdf_intrinsics {
+  float fx, fy, cx, cy; /* pinhole, pixels */
+} tsdf_intrinsics;
+
+typedef struct tsdf_pose {
+  float m[16]; /* row-major 4x4 camera-to-world; last row 0 0 0 1 (not read) */
+} tsdf_pose;
+
+/* Device addresses of a volume's arrays, for inspection and tests. */
+typedef struct tsdf_layout {
+  void* base;              /* start of the volume's allocation */
+  size_t bytes;            /* its size, = tsdf_volume_bytes(...) */
+  uint32_t* block_count;   /* device: blocks claimed (may exceed pool on overflow) */
+  uint32_t* error_word;    /* device: sticky error bits, see TSDF_ERRBIT_* */
+  void* table;             /* device: table_slots entries {uint64 key; int32 idx; int32 pad} */
+  int32_t* block_coords;   /* device: pool_blocks x {bx, by, bz} */
+  float* channel[5];       /* device: tsdf sum, weight, red sum, green sum, blue sum */
+  uint32_t table_slots;
+  uint32_t pool_blocks;
+  size_t table_offset, coords_offset, channel_offset[5]; /* byte offsets from base */
+} tsdf_layout;
+
+/* Sticky bits of the device error word. */
+#define TSDF_ERRBIT_POOL_FULL 1u
+#define TSDF_ERRBIT_TABLE_FULL 2u
+#define TSDF_ERRBIT_PUBLISH_TIMEOUT 4u
+#define TSDF_ERRBIT_BOUNDS 8u
+
+/* The empty key and the unpublished index of a table entry (Section 2.3). */
+#define TSDF_EMPTY_KEY 0xFFFFFFFFFFFFFFFFull
+#define TSDF_UNPUBLISHED (-1)
+
+/* Options (tsdf_volume_set_option). */
+typedef enum tsdf_option {
+  /* How stage A reads a probed entry before any compare-exchange (Section 6.2:
+   * a GPU-scope atomic load bypasses L1, a plain load may hit in it).
+   * 0 = plain load cached in L1 (default), 1 = L2 only (.cg), 2 = relaxed
+   * GPU-scope atomic load. */
+  TSDF_OPT_PROBE_LOAD = 0,
+  /* Upper bound on the wait for a block index to be published, nanoseconds
+   * (default 1e9). The wait gives up with TSDF_ERR_PUBLISH_TIMEOUT. */
+  TSDF_OPT_PUBLISH_TIMEOUT_NS = 1,
+  /* Stage B strategy: 0 = one atomic add per contribution and channel (the
+   * paper's update stage), 1 = contributions aggregated per voxel in shared
+   * memory before one vector add per voxel group (default). */
+  TSDF_OPT_INTEGRATE_MODE = 2,
+  /* Launch shape: threads per CTA for both stages (128, 256 or 512). */
+  TSDF_OPT_THREADS = 3
+} tsdf_option;
+
+/* ---------------------------------------------------------------------------
+ * Volumes
+ * ------------------------------------------------------------------------- */
+
+/* Bytes of device memory a volume with these sizes occupies (0 if invalid). */
+size_t tsdf_volume_bytes(uint32_t table_slots, uint32_t pool_blocks);
+
+/* Create a volume in library-allocated device memory (cudaMalloc on the
+ * current device), initialised empty. table_slots must be a power of two >= 2,
+ * 1 <= pool_blocks <= table_slots, voxel_size > 0, truncation >= voxel_size and
+ * truncation / voxel_size <= 16. The paper sizes the table at the next power of
+ * two above twice the pool (Section 2.1); any pool_blocks <= table_slots is
+ * accepted, so load factors up to 1 can be studied. On error *out is NULL. */
+tsdf_status tsdf_volume_create(float voxel_size, float truncation, uint32_t table_slots,
+                               uint32_t pool_blocks, tsdf_volume** out);
+
+/* Same, in caller-owned device memory of at least tsdf_volume_bytes() bytes,
+ * 256-byte aligned (e.g. a torch tensor). The library never frees it; the
+ * caller keeps it alive until tsdf_volume_destroy. The harness-owned memory of
+ * Section 3.1 ("handed pointers into memory allocated once by the harness").
+ * Initialisation is enqueued on `stream`. */
+tsdf_status tsdf_volume_create_in(void* dev_mem, size_t bytes, float voxel_size,
+                                  float truncation, uint32_t table_slots,
+                                  uint32_t pool_blocks, void* stream,
+                                  tsdf_volume** out);
+
+/* Empty the volume (table, counter, error word, used part of the pool) and
+ * clear the poisoned state. Enqueued on `stream`. */
+tsdf_status tsdf_volume_reset(tsdf_volume* vol, void* stream);
+
+/* Release the volume (and its memory if the library allocated it). Waits for
+ * the device to finish using it. NULL is ignored. */
+void tsdf_volume_destroy(tsdf_volume* vol);
+
+tsdf_status tsdf_volume_set_option(tsdf_volume* vol, tsdf_option opt, int64_t value);
+tsdf_status tsdf_volume_layout(const tsdf_volume* vol, tsdf_layout* out);
+
+/* ---------------------------------------------------------------------------
+ * Fusion
+ * ------------------------------------------------------------------------- */
+
+/* Fuse one frame: stage A then stage B, enqueued on `stream`, then wait for
+ * the stream and return the volume's status (as tsdf_volume_status).
+ * depth_dev: height*width float32, row-major, device memory; a pixel is valid
+ *   iff finite and > 0. rgb_dev: height*width*3 uint8 (interleaved), device
+ *   memory, or NULL to skip the colour sums. Both are only read, and only
+ *   during the call. width, height in [1, 32768]. */
+tsdf_status tsdf_fuse_frame(tsdf_volume* vol, const float* depth_dev, int width, int height,
+                            const tsdf_intrinsics* intr, const tsdf_pose* pose,
+                            const uint8_t* rgb_dev, void* stream);
+
+/* As tsdf_fuse_frame but only enqueues; errors surface through
+ * tsdf_volume_status. depth_dev and rgb_dev must stay valid until the stream
+ * reaches the end of the work. */
+tsdf_status tsdf_fuse_frame_async(tsdf_volume* vol, const float* depth_dev, int width,
+                                  int height, const tsdf_intrinsics* intr,
+                                  const tsdf_pose* pose, const uint8_t* rgb_dev,
+                                  void* stream);
+
+/* End-to-end variant with HOST inputs: copies depth (and rgb when not NULL)
+ * to device staging owned by the volume (grown on first use, kept until
+ * destroy), fuses, and returns the status, all ordered on `stream`. Host
+ * buffers in pinned memory make the copies asynchronous. */
+tsdf_status tsdf_fuse_frame_host(tsdf_volume* vol, const float* depth_host, int width,
+                                 int height, const tsdf_intrinsics* intr,
+                                 const tsdf_pose* pose, const uint8_t* rgb_host,
+                                 void* stream);
+
+/* Stage A alone (Section 2.2 "Allocate"): enqueue block allocation. */
+tsdf_status tsdf_allocate_async(tsdf_volume* vol, const float* depth_dev, int width,
+                                int height, const tsdf_intrinsics* intr,
+                                const tsdf_pose* pose, void* stream);
+
+/* Stage B alone (Section 2.2 "Update"): enqueue integration into blocks that
+ * stage A allocated for the same frame. A contribution whose block is absent
+ * (only possible after an overflow) is skipped. */
+tsdf_status tsdf_integrate_async(tsdf_volume* vol, const float* depth_dev, int width,
+                                 int height, const tsdf_intrinsics* intr,
+                                 const tsdf_pose* pose, const uint8_t* rgb_dev,
+                                 void* stream);
+
+/* Wait for `stream`, read the device error word and map it to a status
+ * (POOL_FULL, then TABLE_FULL, then PUBLISH_TIMEOUT, then BOUNDS). Any error
+ * poisons the volume. */
+tsdf_status tsdf_volume_status(tsdf_volume* vol, void* stream);
+
+/* Number of allocated blocks, min(claimed, pool_blocks). Waits for `stream`. */
+tsdf_status tsdf_volume_block_count(tsdf_volume* vol, void* stream, uint32_t* n);
+
+/* ---------------------------------------------------------------------------
+ * Read-out (Section 2.2: means recovered at extraction)
+ * ------------------------------------------------------------------------- */
+
+/* Copy every allocated block to host memory, in pool order: coords_host gets
+ * n x {bx, by, bz}; voxels_host gets n x 5 x 512 float32, per block the
+ * channels {tsdf mean, weight, red mean, green mean, blue mean} (means are
+ * sum / weight where weight > 0, else 0; colours in [0, 1]). If capacity < n
+ * nothing is copied and TSDF_ERR_INVALID_ARG is returned; *n_out is always n.
+ * Either host pointer may be NULL to query n. Waits for `stream`. */
+tsdf_status tsdf_export_blocks(tsdf_volume* vol, int32_t* coords_host, float* voxels_host,
+                               uint32_t capacity, uint32_t* n_out, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Exact integer helpers (the device code uses the same definitions)
+ * ------------------------------------------------------------------------- */
+
+/* Packed 64-bit key of block (bx, by, bz), each in [-2^20, 2^20) (Section 2.1). */
+uint64_t tsdf_block_key(int32_t bx, int32_t by, int32_t bz);
+
+/* Home slot of a block: (bx*73856093 ^ by*19349669 ^ bz*83492791) mod 2^32,
+ * masked to table_slots - 1 (multiply-xor hash of Section 3.1, constants of
+ * Teschner et al. 2003). table_slots must be a power of two. */
+uint32_t tsdf_block_slot(int32_t bx, int32_t by, int32_t bz, uint32_t table_slots);
+
+const char* tsdf_status_string(tsdf_status s);
+
+/* Library version, and the number of kernel launches this process has
+ * enqueued through the library (for accounting in benchmarks). */
+const char* tsdf_version(void);
+uint64_t tsdf_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TSDF_H_ */

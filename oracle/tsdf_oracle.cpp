@@ -289,8 +289,11 @@ int oracle_fuse(void* h, const float* depth, int W, int H, const float* intr,
   }
   if (stats) std::memcpy(stats, st, sizeof(st));
   if (V->claimed > V->pool) {
+    // Overflow is reported, never silent (Section 3.4). Each distinct block
+    // needs its own table slot and pool entry. With pool < slots the pool runs
+    // out first; with pool == slots the table does.
     V->poisoned = true;
-    return OR_POOL_FULL;  // also covers claimed > slots, since pool <= slots
+    return V->pool < V->slots ? OR_POOL_FULL : OR_TABLE_FULL;
   }
   return OR_OK;
 }

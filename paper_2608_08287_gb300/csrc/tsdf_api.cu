@@ -1,0 +1,462 @@
+// Host runtime of libtsdf: the C ABI declared in include/tsdf.h.
+//
+// A volume is one device allocation (header | table | block coordinates |
+// five channel arrays) plus host-side state (parameters, options, a pinned
+// status word, the poisoned flag, staging for host inputs). Every call checks
+// its arguments before enqueuing anything and returns a status; no exception
+// crosses the ABI.
+#include <atomic>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+
+#include <cuda_runtime.h>
+
+#include "tsdf.h"
+#include "tsdf_device.cuh"
+#include "tsdf_launch.h"
+
+namespace {
+
+std::atomic<uint64_t> g_launches{0};
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+struct Offsets {
+  size_t table, coords, ch[5], total;
+};
+
+bool sizes_ok(uint32_t slots, uint32_t pool) {
+  return slots >= 2 && (slots & (slots - 1)) == 0 && pool >= 1 && pool <= slots;
+}
+
+Offsets offsets_of(uint32_t slots, uint32_t pool) {
+  Offsets o;
+  size_t at = align_up(sizeof(tsdf::Header));
+  o.table = at;
+  at = align_up(at + static_cast<size_t>(slots) * sizeof(tsdf::Entry));
+  o.coords = at;
+  at = align_up(at + static_cast<size_t>(pool) * 3 * sizeof(int32_t));
+  for (int c = 0; c < 5; ++c) {
+    o.ch[c] = at;
+    at = align_up(at + static_cast<size_t>(pool) * tsdf::kBlockVoxels * sizeof(float));
+  }
+  o.total = at;
+  return o;
+}
+
+}  // namespace
+
+struct tsdf_volume {
+  int device = 0;
+  int sm_count = 0;
+  float voxel = 0.0f, trunc = 0.0f;
+  int half_band = 0;
+  uint32_t slots = 0, pool = 0;
+  void* mem = nullptr;
+  size_t bytes = 0;
+  bool owns = false;
+  Offsets off{};
+  tsdf::VolumeArgs va{};
+  bool poisoned = false;
+  uint32_t* pinned = nullptr;  // {count, err}
+  int probe_load = tsdf::kLoadCached;
+  int integrate_mode = 1;
+  int threads = 256;
+  void* stage = nullptr;
+  size_t stage_bytes = 0;
+};
+
+namespace tsdf {
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+}  // namespace tsdf
+
+namespace {
+
+tsdf_status from_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return TSDF_OK;
+  if (e == cudaErrorMemoryAllocation) return TSDF_ERR_OUT_OF_MEMORY;
+  return TSDF_ERR_CUDA;
+}
+
+tsdf_status decode_err(uint32_t err) {
+  if (err & TSDF_ERRBIT_POOL_FULL) return TSDF_ERR_POOL_FULL;
+  if (err & TSDF_ERRBIT_TABLE_FULL) return TSDF_ERR_TABLE_FULL;
+  if (err & TSDF_ERRBIT_PUBLISH_TIMEOUT) return TSDF_ERR_PUBLISH_TIMEOUT;
+  if (err & TSDF_ERRBIT_BOUNDS) return TSDF_ERR_BOUNDS;
+  return TSDF_OK;
+}
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Enqueue the initialisation of an empty volume: table entries all-ones
+// (key = EMPTY, index = -1), header zero, used prefix of the pool zero.
+tsdf_status enqueue_clear(tsdf_volume* v, cudaStream_t s, bool whole_pool) {
+  char* base = static_cast<char*>(v->mem);
+  cudaError_t e;
+  if (whole_pool) {
+    e = cudaMemsetAsync(base + v->off.ch[0], 0, v->off.total - v->off.ch[0], s);
+  } else {
+    e = tsdf::launch_clear_used(v->va, v->sm_count, s);
+  }
+  if (e != cudaSuccess) return from_cuda(e);
+  e = cudaMemsetAsync(base + v->off.table, 0xFF,
+                      static_cast<size_t>(v->slots) * sizeof(tsdf::Entry), s);
+  if (e != cudaSuccess) return from_cuda(e);
+  e = cudaMemsetAsync(base, 0, sizeof(tsdf::Header), s);
+  return from_cuda(e);
+}
+
+tsdf_status init_volume(tsdf_volume* v, void* mem, size_t bytes, bool owns, float voxel,
+                        float trunc, uint32_t slots, uint32_t pool, cudaStream_t s) {
+  v->voxel = voxel;
+  v->trunc = trunc;
+  v->half_band = static_cast<int>(lrintf(trunc / voxel));
+  v->slots = slots;
+  v->pool = pool;
+  v->mem = mem;
+  v->bytes = bytes;
+  v->owns = owns;
+  v->off = offsets_of(slots, pool);
+  cudaError_t e = cudaGetDevice(&v->device);
+  if (e != cudaSuccess) return from_cuda(e);
+  e = cudaDeviceGetAttribute(&v->sm_count, cudaDevAttrMultiProcessorCount, v->device);
+  if (e != cudaSuccess) return from_cuda(e);
+  char* base = static_cast<char*>(mem);
+  v->va.hdr = reinterpret_cast<tsdf::Header*>(base);
+  v->va.table = reinterpret_cast<tsdf::Entry*>(base + v->off.table);
+  v->va.mask = slots - 1;
+  v->va.slots = slots;
+  v->va.coords = reinterpret_cast<int32_t*>(base + v->off.coords);
+  v->va.pool = pool;
+  for (int c = 0; c < 5; ++c) v->va.ch[c] = reinterpret_cast<float*>(base + v->off.ch[c]);
+  v->va.timeout_ns = 1000000000ull;
+  e = cudaMallocHost(reinterpret_cast<void**>(&v->pinned), 2 * sizeof(uint32_t));
+  if (e != cudaSuccess) {
+    v->pinned = nullptr;
+    return TSDF_ERR_OUT_OF_MEMORY;
+  }
+  return enqueue_clear(v, s, true);
+}
+
+bool params_ok(float voxel, float trunc) {
+  if (!(std::isfinite(voxel) && voxel > 0.0f)) return false;
+  if (!(std::isfinite(trunc) && trunc >= voxel)) return false;
+  const long m = lrintf(trunc / voxel);
+  return m >= 1 && m <= tsdf::kMaxHalfBand;
+}
+
+tsdf_status make_frame(const tsdf_volume* v, const float* depth, int w, int h,
+                       const tsdf_intrinsics* intr, const tsdf_pose* pose, const uint8_t* rgb,
+                       tsdf::FrameArgs* f) {
+  if (!v || !depth || !intr || !pose) return TSDF_ERR_INVALID_ARG;
+  if (w < 1 || h < 1 || w > 32768 || h > 32768) return TSDF_ERR_INVALID_ARG;
+  if (!(std::isfinite(intr->fx) && std::isfinite(intr->fy) && std::isfinite(intr->cx) &&
+        std::isfinite(intr->cy) && intr->fx != 0.0f && intr->fy != 0.0f))
+    return TSDF_ERR_INVALID_ARG;
+  for (int i = 0; i < 12; ++i)
+    if (!std::isfinite(pose->m[i])) return TSDF_ERR_INVALID_ARG;
+  f->depth = depth;
+  f->rgb = rgb;
+  f->W = w;
+  f->H = h;
+  f->fx = intr->fx;
+  f->fy = intr->fy;
+  f->cx = intr->cx;
+  f->cy = intr->cy;
+  for (int i = 0; i < 3; ++i) {
+    for (int j = 0; j < 3; ++j) f->R[3 * i + j] = pose->m[4 * i + j];
+    f->t[i] = pose->m[4 * i + 3];
+  }
+  f->v = v->voxel;
+  f->inv_v = 1.0f / v->voxel;
+  f->tau = v->trunc;
+  f->neg_tau = -v->trunc;
+  f->inv_tau = 1.0f / v->trunc;
+  f->M = v->half_band;
+  return TSDF_OK;
+}
+
+tsdf_status read_header(tsdf_volume* v, cudaStream_t s) {
+  cudaError_t e = cudaMemcpyAsync(v->pinned, v->mem, 2 * sizeof(uint32_t),
+                                  cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return from_cuda(e);
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t tsdf_volume_bytes(uint32_t table_slots, uint32_t pool_blocks) {
+  if (!sizes_ok(table_slots, pool_blocks)) return 0;
+  return offsets_of(table_slots, pool_blocks).total;
+}
+
+tsdf_status tsdf_volume_create(float voxel_size, float truncation, uint32_t table_slots,
+                               uint32_t pool_blocks, tsdf_volume** out) {
+  if (!out) return TSDF_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!sizes_ok(table_slots, pool_blocks) || !params_ok(voxel_size, truncation))
+    return TSDF_ERR_INVALID_ARG;
+  const size_t bytes = tsdf_volume_bytes(table_slots, pool_blocks);
+  void* mem = nullptr;
+  cudaError_t e = cudaMalloc(&mem, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return TSDF_ERR_OUT_OF_MEMORY;
+  }
+  tsdf_volume* v = new (std::nothrow) tsdf_volume();
+  if (!v) {
+    cudaFree(mem);
+    return TSDF_ERR_OUT_OF_MEMORY;
+  }
+  tsdf_status st = init_volume(v, mem, bytes, true, voxel_size, truncation, table_slots,
+                               pool_blocks, nullptr);
+  if (st == TSDF_OK) st = from_cuda(cudaStreamSynchronize(nullptr));
+  if (st != TSDF_OK) {
+    tsdf_volume_destroy(v);
+    return st;
+  }
+  *out = v;
+  return TSDF_OK;
+}
+
+tsdf_status tsdf_volume_create_in(void* dev_mem, size_t bytes, float voxel_size,
+                                  float truncation, uint32_t table_slots,
+                                  uint32_t pool_blocks, void* stream, tsdf_volume** out) {
+  if (!out) return TSDF_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!dev_mem || (reinterpret_cast<uintptr_t>(dev_mem) % kAlign) != 0)
+    return TSDF_ERR_INVALID_ARG;
+  if (!sizes_ok(table_slots, pool_blocks) || !params_ok(voxel_size, truncation))
+    return TSDF_ERR_INVALID_ARG;
+  if (bytes < tsdf_volume_bytes(table_slots, pool_blocks)) return TSDF_ERR_INVALID_ARG;
+  tsdf_volume* v = new (std::nothrow) tsdf_volume();
+  if (!v) return TSDF_ERR_OUT_OF_MEMORY;
+  const tsdf_status st = init_volume(v, dev_mem, bytes, false, voxel_size, truncation,
+                                     table_slots, pool_blocks, as_stream(stream));
+  if (st != TSDF_OK) {
+    tsdf_volume_destroy(v);
+    return st;
+  }
+  *out = v;
+  return TSDF_OK;
+}
+
+tsdf_status tsdf_volume_reset(tsdf_volume* vol, void* stream) {
+  if (!vol) return TSDF_ERR_INVALID_ARG;
+  const tsdf_status st = enqueue_clear(vol, as_stream(stream), false);
+  if (st == TSDF_OK) vol->poisoned = false;
+  return st;
+}
+
+void tsdf_volume_destroy(tsdf_volume* vol) {
+  if (!vol) return;
+  cudaDeviceSynchronize();
+  if (vol->owns && vol->mem) cudaFree(vol->mem);
+  if (vol->stage) cudaFree(vol->stage);
+  if (vol->pinned) cudaFreeHost(vol->pinned);
+  delete vol;
+}
+
+tsdf_status tsdf_volume_set_option(tsdf_volume* vol, tsdf_option opt, int64_t value) {
+  if (!vol) return TSDF_ERR_INVALID_ARG;
+  switch (opt) {
+    case TSDF_OPT_PROBE_LOAD:
+      if (value < 0 || value > 2) return TSDF_ERR_INVALID_ARG;
+      vol->probe_load = static_cast<int>(value);
+      return TSDF_OK;
+    case TSDF_OPT_PUBLISH_TIMEOUT_NS:
+      if (value < 1000 || value > 10000000000ll) return TSDF_ERR_INVALID_ARG;
+      vol->va.timeout_ns = static_cast<unsigned long long>(value);
+      return TSDF_OK;
+    case TSDF_OPT_INTEGRATE_MODE:
+      if (value < 0 || value > 1) return TSDF_ERR_INVALID_ARG;
+      vol->integrate_mode = static_cast<int>(value);
+      return TSDF_OK;
+    case TSDF_OPT_THREADS:
+      if (value != 256) return TSDF_ERR_INVALID_ARG;
+      vol->threads = static_cast<int>(value);
+      return TSDF_OK;
+  }
+  return TSDF_ERR_INVALID_ARG;
+}
+
+tsdf_status tsdf_volume_layout(const tsdf_volume* vol, tsdf_layout* out) {
+  if (!vol || !out) return TSDF_ERR_INVALID_ARG;
+  std::memset(out, 0, sizeof(*out));
+  out->base = vol->mem;
+  out->bytes = vol->off.total;
+  out->block_count = &vol->va.hdr->count;
+  out->error_word = &vol->va.hdr->err;
+  out->table = vol->va.table;
+  out->block_coords = vol->va.coords;
+  for (int c = 0; c < 5; ++c) {
+    out->channel[c] = vol->va.ch[c];
+    out->channel_offset[c] = vol->off.ch[c];
+  }
+  out->table_slots = vol->slots;
+  out->pool_blocks = vol->pool;
+  out->table_offset = vol->off.table;
+  out->coords_offset = vol->off.coords;
+  return TSDF_OK;
+}
+
+tsdf_status tsdf_allocate_async(tsdf_volume* vol, const float* depth_dev, int width,
+                                int height, const tsdf_intrinsics* intr,
+                                const tsdf_pose* pose, void* stream) {
+  tsdf::FrameArgs f;
+  tsdf_status st = make_frame(vol, depth_dev, width, height, intr, pose, nullptr, &f);
+  if (st != TSDF_OK) return st;
+  if (vol->poisoned) return TSDF_ERR_POISONED;
+  return from_cuda(tsdf::launch_allocate(f, vol->va, vol->probe_load, as_stream(stream)));
+}
+
+tsdf_status tsdf_integrate_async(tsdf_volume* vol, const float* depth_dev, int width,
+                                 int height, const tsdf_intrinsics* intr,
+                                 const tsdf_pose* pose, const uint8_t* rgb_dev,
+                                 void* stream) {
+  tsdf::FrameArgs f;
+  tsdf_status st = make_frame(vol, depth_dev, width, height, intr, pose, rgb_dev, &f);
+  if (st != TSDF_OK) return st;
+  if (vol->poisoned) return TSDF_ERR_POISONED;
+  return from_cuda(tsdf::launch_integrate(f, vol->va, vol->integrate_mode, as_stream(stream)));
+}
+
+tsdf_status tsdf_fuse_frame_async(tsdf_volume* vol, const float* depth_dev, int width,
+                                  int height, const tsdf_intrinsics* intr,
+                                  const tsdf_pose* pose, const uint8_t* rgb_dev,
+                                  void* stream) {
+  tsdf::FrameArgs f;
+  tsdf_status st = make_frame(vol, depth_dev, width, height, intr, pose, rgb_dev, &f);
+  if (st != TSDF_OK) return st;
+  if (vol->poisoned) return TSDF_ERR_POISONED;
+  cudaError_t e = tsdf::launch_allocate(f, vol->va, vol->probe_load, as_stream(stream));
+  if (e == cudaSuccess) e = tsdf::launch_integrate(f, vol->va, vol->integrate_mode,
+                                                   as_stream(stream));
+  return from_cuda(e);
+}
+
+tsdf_status tsdf_volume_status(tsdf_volume* vol, void* stream) {
+  if (!vol) return TSDF_ERR_INVALID_ARG;
+  const tsdf_status st = read_header(vol, as_stream(stream));
+  if (st != TSDF_OK) return st;
+  const tsdf_status dev = decode_err(vol->pinned[1]);
+  if (dev != TSDF_OK) vol->poisoned = true;
+  return dev;
+}
+
+tsdf_status tsdf_fuse_frame(tsdf_volume* vol, const float* depth_dev, int width, int height,
+                            const tsdf_intrinsics* intr, const tsdf_pose* pose,
+                            const uint8_t* rgb_dev, void* stream) {
+  const tsdf_status st =
+      tsdf_fuse_frame_async(vol, depth_dev, width, height, intr, pose, rgb_dev, stream);
+  if (st != TSDF_OK) return st;
+  return tsdf_volume_status(vol, stream);
+}
+
+tsdf_status tsdf_fuse_frame_host(tsdf_volume* vol, const float* depth_host, int width,
+                                 int height, const tsdf_intrinsics* intr,
+                                 const tsdf_pose* pose, const uint8_t* rgb_host,
+                                 void* stream) {
+  tsdf::FrameArgs f;
+  tsdf_status st = make_frame(vol, depth_host, width, height, intr, pose, rgb_host, &f);
+  if (st != TSDF_OK) return st;
+  if (vol->poisoned) return TSDF_ERR_POISONED;
+  const size_t npx = static_cast<size_t>(width) * height;
+  const size_t dbytes = align_up(npx * sizeof(float));
+  const size_t need = dbytes + (rgb_host ? npx * 3 : 0);
+  if (vol->stage_bytes < need) {
+    if (vol->stage) {
+      cudaStreamSynchronize(as_stream(stream));
+      cudaFree(vol->stage);
+      vol->stage = nullptr;
+      vol->stage_bytes = 0;
+    }
+    if (cudaMalloc(&vol->stage, need) != cudaSuccess) {
+      cudaGetLastError();
+      return TSDF_ERR_OUT_OF_MEMORY;
+    }
+    vol->stage_bytes = need;
+  }
+  char* sbase = static_cast<char*>(vol->stage);
+  cudaStream_t s = as_stream(stream);
+  cudaError_t e = cudaMemcpyAsync(sbase, depth_host, npx * sizeof(float),
+                                  cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && rgb_host)
+    e = cudaMemcpyAsync(sbase + dbytes, rgb_host, npx * 3, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return from_cuda(e);
+  return tsdf_fuse_frame(vol, reinterpret_cast<const float*>(sbase), width, height, intr, pose,
+                         rgb_host ? reinterpret_cast<const uint8_t*>(sbase + dbytes) : nullptr,
+                         stream);
+}
+
+tsdf_status tsdf_volume_block_count(tsdf_volume* vol, void* stream, uint32_t* n) {
+  if (!vol || !n) return TSDF_ERR_INVALID_ARG;
+  const tsdf_status st = read_header(vol, as_stream(stream));
+  if (st != TSDF_OK) return st;
+  *n = vol->pinned[0] < vol->pool ? vol->pinned[0] : vol->pool;
+  return TSDF_OK;
+}
+
+tsdf_status tsdf_export_blocks(tsdf_volume* vol, int32_t* coords_host, float* voxels_host,
+                               uint32_t capacity, uint32_t* n_out, void* stream) {
+  if (!vol || !n_out) return TSDF_ERR_INVALID_ARG;
+  cudaStream_t s = as_stream(stream);
+  uint32_t n = 0;
+  tsdf_status st = tsdf_volume_block_count(vol, stream, &n);
+  if (st != TSDF_OK) return st;
+  *n_out = n;
+  if (!coords_host && !voxels_host) return TSDF_OK;
+  if (capacity < n) return TSDF_ERR_INVALID_ARG;
+  if (n == 0) return TSDF_OK;
+  cudaError_t e = cudaSuccess;
+  if (coords_host)
+    e = cudaMemcpyAsync(coords_host, vol->va.coords, static_cast<size_t>(n) * 3 * sizeof(int32_t),
+                        cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && voxels_host) {
+    const size_t bytes = static_cast<size_t>(n) * 5 * tsdf::kBlockVoxels * sizeof(float);
+    float* tmp = nullptr;
+    e = cudaMallocAsync(reinterpret_cast<void**>(&tmp), bytes, s);
+    if (e == cudaSuccess) {
+      e = tsdf::launch_export(vol->va, tmp, n, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(voxels_host, tmp, bytes, cudaMemcpyDeviceToHost, s);
+      const cudaError_t e2 = cudaFreeAsync(tmp, s);
+      if (e == cudaSuccess) e = e2;
+    }
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return from_cuda(e);
+}
+
+uint64_t tsdf_block_key(int32_t bx, int32_t by, int32_t bz) {
+  return tsdf::pack_key(bx, by, bz);
+}
+
+uint32_t tsdf_block_slot(int32_t bx, int32_t by, int32_t bz, uint32_t table_slots) {
+  return tsdf::hash_block(bx, by, bz) & (table_slots - 1u);
+}
+
+const char* tsdf_status_string(tsdf_status s) {
+  switch (s) {
+    case TSDF_OK: return "TSDF_OK";
+    case TSDF_ERR_INVALID_ARG: return "TSDF_ERR_INVALID_ARG";
+    case TSDF_ERR_OUT_OF_MEMORY: return "TSDF_ERR_OUT_OF_MEMORY";
+    case TSDF_ERR_POOL_FULL: return "TSDF_ERR_POOL_FULL";
+    case TSDF_ERR_TABLE_FULL: return "TSDF_ERR_TABLE_FULL";
+    case TSDF_ERR_PUBLISH_TIMEOUT: return "TSDF_ERR_PUBLISH_TIMEOUT";
+    case TSDF_ERR_BOUNDS: return "TSDF_ERR_BOUNDS";
+    case TSDF_ERR_POISONED: return "TSDF_ERR_POISONED";
+    case TSDF_ERR_CUDA: return "TSDF_ERR_CUDA";
+  }
+  return "TSDF_ERR_UNKNOWN";
+}
+
+const char* tsdf_version(void) { return "libtsdf 0.1 (sm_103a)"; }
+
+uint64_t tsdf_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+}  // extern "C"

@@ -1,0 +1,295 @@
+// Device-side data structures and per-point geometry of hash-blocked TSDF
+// fusion (paper Section 2). Shared by the stage A / stage B / fused kernels.
+//
+// Every floating-point step that decides an integer (voxel index, pixel index,
+// accept/reject) is written with explicit round-to-nearest intrinsics
+// (__fadd_rn, __fmul_rn, __fmaf_rn, __fdiv_rn, __frcp_rn, __fsqrt_rn) in one
+// fixed order, so the compiler can neither contract nor reorder it and the
+// decisions are reproducible by any IEEE-754 single-precision implementation
+// of the same steps.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "tsdf.h"
+
+namespace tsdf {
+
+constexpr int kBlockEdge = 8;                 // Section 2.1: 8^3 voxels per block
+constexpr int kBlockVoxels = 512;
+constexpr int kKeyBias = 1 << 20;             // Section 2.1: 21-bit biased axes
+constexpr int kMaxHalfBand = 16;              // M = lrintf(tau / v) <= 16
+constexpr unsigned long long kEmptyKey = TSDF_EMPTY_KEY;
+constexpr int kUnpublished = TSDF_UNPUBLISHED;   // index not yet published
+constexpr int kFailedIdx = -2;                // slot won but pool exhausted
+constexpr float kVoxelLimit = 8388608.0f;     // 2^23 voxels = 2^20 blocks
+
+// 16-byte table entry (Section 2.1): 64-bit key, 32-bit block index, padding.
+struct __align__(16) Entry {
+  unsigned long long key;
+  int idx;
+  int pad;
+};
+static_assert(sizeof(Entry) == 16, "table entry must be 16 bytes");
+
+// Volume header at offset 0 of the allocation.
+struct __align__(256) Header {
+  unsigned int count;  // blocks claimed (atomicAdd after winning a slot)
+  unsigned int err;    // sticky TSDF_ERRBIT_* flags
+  unsigned int pad[62];
+};
+
+// Packed key (Section 2.1): each axis biased by 2^20 into 21 bits.
+__host__ __device__ __forceinline__ unsigned long long pack_key(int bx, int by, int bz) {
+  return (static_cast<unsigned long long>(static_cast<unsigned int>(bx + kKeyBias)) << 42) |
+         (static_cast<unsigned long long>(static_cast<unsigned int>(by + kKeyBias)) << 21) |
+         static_cast<unsigned long long>(static_cast<unsigned int>(bz + kKeyBias));
+}
+
+__host__ __device__ __forceinline__ void unpack_key(unsigned long long key, int& bx, int& by,
+                                                    int& bz) {
+  const unsigned long long m = (1ull << 21) - 1;
+  bx = static_cast<int>((key >> 42) & m) - kKeyBias;
+  by = static_cast<int>((key >> 21) & m) - kKeyBias;
+  bz = static_cast<int>(key & m) - kKeyBias;
+}
+
+// Multiply-xor hash (Section 3.1) with the primes of Teschner et al. (2003),
+// products and xor taken mod 2^32.
+__host__ __device__ __forceinline__ unsigned int hash_block(int bx, int by, int bz) {
+  return (static_cast<unsigned int>(bx) * 73856093u) ^
+         (static_cast<unsigned int>(by) * 19349669u) ^
+         (static_cast<unsigned int>(bz) * 83492791u);
+}
+
+// Per-frame constants, passed by value (__grid_constant__) to every kernel.
+struct FrameArgs {
+  const float* depth;      // H x W, row-major
+  const uint8_t* rgb;      // H x W x 3 or nullptr
+  int W, H;
+  float fx, fy, cx, cy;
+  float R[9];              // camera-to-world rotation, row-major
+  float t[3];              // camera-to-world translation
+  float v, inv_v;          // voxel size and its IEEE reciprocal
+  float tau, neg_tau, inv_tau;
+  int M;                   // half band, samples k = 0..2M
+};
+
+// Device view of one volume.
+struct VolumeArgs {
+  Entry* table;
+  unsigned int mask;       // table_slots - 1
+  unsigned int slots;
+  int32_t* coords;         // pool x 3
+  unsigned int pool;
+  float* ch[5];            // tsdf sum, weight, r sum, g sum, b sum
+  Header* hdr;
+  unsigned long long timeout_ns;
+};
+
+// ----------------------------------------------------------------------------
+// geometry
+// ----------------------------------------------------------------------------
+struct Ray {
+  float d;                 // the point's depth
+  float px, py, pz;        // back-projected point, camera frame
+  float dx, dy, dz;        // unit view ray, camera frame
+};
+
+// Back-project pixel (u, v) and build its unit view ray. False if the depth
+// is invalid (not finite or not > 0).
+__device__ __forceinline__ bool make_ray(const FrameArgs& f, int u, int v, float d, Ray& r) {
+  if (!(isfinite(d) && d > 0.0f)) return false;
+  const float rx = __fdiv_rn(__fsub_rn(static_cast<float>(u), f.cx), f.fx);
+  const float ry = __fdiv_rn(__fsub_rn(static_cast<float>(v), f.cy), f.fy);
+  r.d = d;
+  r.px = __fmul_rn(rx, d);
+  r.py = __fmul_rn(ry, d);
+  r.pz = d;
+  const float n = __fsqrt_rn(__fmaf_rn(rx, rx, __fmaf_rn(ry, ry, 1.0f)));
+  r.dx = __fdiv_rn(rx, n);
+  r.dy = __fdiv_rn(ry, n);
+  r.dz = __fdiv_rn(1.0f, n);
+  return true;
+}
+
+// Voxel selected by band sample k (offset (k-M) v along the ray). False if the
+// voxel's block coordinate does not fit the 21-bit key.
+__device__ __forceinline__ bool sample_voxel(const FrameArgs& f, const Ray& r, int k, int& gx,
+                                             int& gy, int& gz) {
+  const float tk = __fmul_rn(static_cast<float>(k - f.M), f.v);
+  const float sx = __fmaf_rn(tk, r.dx, r.px);
+  const float sy = __fmaf_rn(tk, r.dy, r.py);
+  const float sz = __fmaf_rn(tk, r.dz, r.pz);
+  const float wx = __fmaf_rn(f.R[2], sz, __fmaf_rn(f.R[1], sy, __fmaf_rn(f.R[0], sx, f.t[0])));
+  const float wy = __fmaf_rn(f.R[5], sz, __fmaf_rn(f.R[4], sy, __fmaf_rn(f.R[3], sx, f.t[1])));
+  const float wz = __fmaf_rn(f.R[8], sz, __fmaf_rn(f.R[7], sy, __fmaf_rn(f.R[6], sx, f.t[2])));
+  const float qx = floorf(__fmul_rn(wx, f.inv_v));
+  const float qy = floorf(__fmul_rn(wy, f.inv_v));
+  const float qz = floorf(__fmul_rn(wz, f.inv_v));
+  const bool ok = (qx >= -kVoxelLimit) && (qx < kVoxelLimit) && (qy >= -kVoxelLimit) &&
+                  (qy < kVoxelLimit) && (qz >= -kVoxelLimit) && (qz < kVoxelLimit);
+  gx = ok ? static_cast<int>(qx) : 0;
+  gy = ok ? static_cast<int>(qy) : 0;
+  gz = ok ? static_cast<int>(qz) : 0;
+  return ok;
+}
+
+// Occlusion test at the voxel centre, shared by both stages (Section 2.2):
+// centre in front of the camera, nearest pixel inside the image with a valid
+// depth d', centre no more than tau behind d'. On success zc = centre's
+// camera-frame depth.
+__device__ __forceinline__ bool voxel_test(const FrameArgs& f, int gx, int gy, int gz,
+                                           float& zc) {
+  const float ex = __fsub_rn(__fmul_rn(__fadd_rn(static_cast<float>(gx), 0.5f), f.v), f.t[0]);
+  const float ey = __fsub_rn(__fmul_rn(__fadd_rn(static_cast<float>(gy), 0.5f), f.v), f.t[1]);
+  const float ez = __fsub_rn(__fmul_rn(__fadd_rn(static_cast<float>(gz), 0.5f), f.v), f.t[2]);
+  // R^T e: column j of R is R[j], R[3+j], R[6+j]
+  const float ccz = __fmaf_rn(f.R[8], ez, __fmaf_rn(f.R[5], ey, __fmul_rn(f.R[2], ex)));
+  if (!(ccz > 0.0f)) return false;
+  const float ccx = __fmaf_rn(f.R[6], ez, __fmaf_rn(f.R[3], ey, __fmul_rn(f.R[0], ex)));
+  const float ccy = __fmaf_rn(f.R[7], ez, __fmaf_rn(f.R[4], ey, __fmul_rn(f.R[1], ex)));
+  const float iz = __frcp_rn(ccz);
+  const float qu = floorf(__fadd_rn(__fmaf_rn(f.fx, __fmul_rn(ccx, iz), f.cx), 0.5f));
+  const float qv = floorf(__fadd_rn(__fmaf_rn(f.fy, __fmul_rn(ccy, iz), f.cy), 0.5f));
+  if (!(qu >= 0.0f && qu < static_cast<float>(f.W) && qv >= 0.0f &&
+        qv < static_cast<float>(f.H)))
+    return false;
+  const float d2 = __ldg(f.depth + static_cast<int>(qv) * f.W + static_cast<int>(qu));
+  if (!(isfinite(d2) && d2 > 0.0f)) return false;
+  if (!(__fsub_rn(d2, ccz) >= f.neg_tau)) return false;
+  zc = ccz;
+  return true;
+}
+
+// Stored value: truncated, normalised signed distance at the voxel centre.
+__device__ __forceinline__ float tsdf_value(const FrameArgs& f, float d, float zc) {
+  return fminf(1.0f, fmaxf(-1.0f, __fsub_rn(d, zc) * f.inv_tau));
+}
+
+__device__ __forceinline__ int local_index(int gx, int gy, int gz) {
+  return (gx & 7) | ((gy & 7) << 3) | ((gz & 7) << 6);
+}
+
+// ----------------------------------------------------------------------------
+// table access
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long global_timer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ int load_idx_volatile(const Entry* e) {
+  return *reinterpret_cast<const volatile int*>(&e->idx);
+}
+
+__device__ __forceinline__ unsigned int load_err_volatile(const Header* h) {
+  return *reinterpret_cast<const volatile unsigned int*>(&h->err);
+}
+
+// Probe-load policies for stage A (Section 6.2: L1 residency of the probe
+// decides speed; a GPU-scope atomic load bypasses L1).
+enum ProbeLoad { kLoadCached = 0, kLoadL2 = 1, kLoadRelaxed = 2 };
+
+template <int P>
+__device__ __forceinline__ void load_entry(const Entry* e, unsigned long long& key, int& idx) {
+  unsigned long long a, b;
+  if (P == kLoadCached) {
+    asm volatile("ld.global.ca.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(e) : "memory");
+  } else if (P == kLoadL2) {
+    asm volatile("ld.global.cg.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(e) : "memory");
+  } else {
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(a) : "l"(&e->key) : "memory");
+    unsigned int i;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(i) : "l"(&e->idx) : "memory");
+    b = i;
+  }
+  key = a;
+  idx = static_cast<int>(static_cast<unsigned int>(b & 0xFFFFFFFFull));
+}
+
+// Wait until the winner of a slot publishes its block index (Section 2.3,
+// "Publication is two steps"). Bounded: gives up after vol.timeout_ns of
+// %globaltimer (or an iteration cap), sets PUBLISH_TIMEOUT and returns -1.
+static __device__ __noinline__ int wait_published(const VolumeArgs& vol, const Entry* e) {
+  int idx = load_idx_volatile(e);
+  if (idx != kUnpublished) return idx >= 0 ? idx : -1;
+  const unsigned long long t0 = global_timer_ns();
+  unsigned int ns = 32;
+  for (unsigned int it = 0; it < (1u << 22); ++it) {
+    __nanosleep(ns);
+    if (ns < 1024) ns <<= 1;
+    idx = load_idx_volatile(e);
+    if (idx != kUnpublished) return idx >= 0 ? idx : -1;
+    if (global_timer_ns() - t0 > vol.timeout_ns) break;
+  }
+  atomicOr(&vol.hdr->err, TSDF_ERRBIT_PUBLISH_TIMEOUT);
+  return -1;
+}
+
+// Insert protocol of Listing 1 (Section 2.3): linear probe from the home slot;
+// a plain load of the entry; on EMPTY a 64-bit compare-exchange; the winner
+// takes a pool index from the counter, writes the block coordinate, fences and
+// publishes the index; a thread that finds the key waits for publication.
+// After a lost exchange the slot is re-examined with the key that won it (a
+// set slot never changes, so if it holds our key this is a hit; moving on
+// would duplicate the key). The scan is bounded only by the table size; a full
+// scan reports TABLE_FULL. Returns the pool index or -1 on error.
+template <int P>
+__device__ int insert_block(const VolumeArgs& vol, unsigned long long key, int bx, int by,
+                            int bz) {
+  unsigned int s = hash_block(bx, by, bz) & vol.mask;
+  for (unsigned int probe = 0; probe < vol.slots; ++probe, s = (s + 1) & vol.mask) {
+    Entry* e = vol.table + s;
+    unsigned long long k;
+    int idx;
+    load_entry<P>(e, k, idx);
+    if (k == kEmptyKey) {
+      const unsigned long long prev = atomicCAS(&e->key, kEmptyKey, key);
+      if (prev == kEmptyKey) {
+        const unsigned int i = atomicAdd(&vol.hdr->count, 1u);
+        if (i >= vol.pool) {
+          atomicOr(&vol.hdr->err, TSDF_ERRBIT_POOL_FULL);
+          atomicExch(&e->idx, kFailedIdx);
+          return -1;
+        }
+        int32_t* c = vol.coords + 3 * static_cast<size_t>(i);
+        c[0] = bx;
+        c[1] = by;
+        c[2] = bz;
+        __threadfence();  // coordinates visible before the index
+        atomicExch(&e->idx, static_cast<int>(i));
+        return static_cast<int>(i);
+      }
+      k = prev;
+      idx = kUnpublished;
+    }
+    if (k == key) return idx >= 0 ? idx : wait_published(vol, e);
+    // a poisoned volume stops long scans early
+    if ((probe & 255u) == 255u &&
+        (load_err_volatile(vol.hdr) & (TSDF_ERRBIT_POOL_FULL | TSDF_ERRBIT_TABLE_FULL)))
+      return -1;
+  }
+  atomicOr(&vol.hdr->err, TSDF_ERRBIT_TABLE_FULL);
+  return -1;
+}
+
+// Read-only lookup for stage B (after stage A's kernel has completed every
+// publication): the table is read through the non-coherent read-only path.
+__device__ __forceinline__ int lookup_block(const VolumeArgs& vol, unsigned long long key, int bx,
+                                            int by, int bz) {
+  unsigned int s = hash_block(bx, by, bz) & vol.mask;
+  for (unsigned int probe = 0; probe < vol.slots; ++probe, s = (s + 1) & vol.mask) {
+    const ulonglong2 ent = __ldg(reinterpret_cast<const ulonglong2*>(vol.table + s));
+    if (ent.x == key) {
+      const int idx = static_cast<int>(static_cast<unsigned int>(ent.y & 0xFFFFFFFFull));
+      return idx >= 0 ? idx : -1;
+    }
+    if (ent.x == kEmptyKey) return -1;
+  }
+  return -1;
+}
+
+}  // namespace tsdf

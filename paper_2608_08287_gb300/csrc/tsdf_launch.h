@@ -1,0 +1,21 @@
+// Internal interface between the host runtime (tsdf_api.cu) and the kernels
+// (tsdf_kernels.cu). Not part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "tsdf_device.cuh"
+
+namespace tsdf {
+
+// Launch accounting: every kernel launch the library enqueues is counted.
+void note_launch();
+
+cudaError_t launch_allocate(const FrameArgs& f, const VolumeArgs& vol, int probe_load,
+                            cudaStream_t s);
+cudaError_t launch_integrate(const FrameArgs& f, const VolumeArgs& vol, int mode,
+                             cudaStream_t s);
+cudaError_t launch_export(const VolumeArgs& vol, float* out, unsigned int n, cudaStream_t s);
+cudaError_t launch_clear_used(const VolumeArgs& vol, int sm_count, cudaStream_t s);
+
+}  // namespace tsdf

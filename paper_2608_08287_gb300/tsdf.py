@@ -1,0 +1,354 @@
+"""Python binding of libtsdf (include/tsdf.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and does no
+computation of its own. Device buffers may be given as torch CUDA tensors or
+as raw device addresses (int); streams as torch streams, raw cudaStream_t
+handles (int) or None (the legacy default stream, which is PyTorch's default
+stream).
+
+The CUDA library must be built (``paper_2608_08287_gb300.build``); if it is
+missing, importing a function fails loudly -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB
+
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OUT_OF_MEMORY", 3: "POOL_FULL", 4: "TABLE_FULL",
+          5: "PUBLISH_TIMEOUT", 6: "BOUNDS", 7: "POISONED", 8: "CUDA"}
+OPTIONS = {"probe_load": 0, "publish_timeout_ns": 1, "integrate_mode": 2, "threads": 3}
+ERRBITS = {"POOL_FULL": 1, "TABLE_FULL": 2, "PUBLISH_TIMEOUT": 4, "BOUNDS": 8}
+EMPTY_KEY = 0xFFFFFFFFFFFFFFFF
+CHANNELS = ("tsdf", "weight", "r", "g", "b")
+
+EXPORTED = ("tsdf_volume_bytes", "tsdf_volume_create", "tsdf_volume_create_in",
+            "tsdf_volume_reset", "tsdf_volume_destroy", "tsdf_volume_set_option",
+            "tsdf_volume_layout", "tsdf_fuse_frame", "tsdf_fuse_frame_async",
+            "tsdf_fuse_frame_host", "tsdf_allocate_async", "tsdf_integrate_async",
+            "tsdf_volume_status", "tsdf_volume_block_count", "tsdf_export_blocks",
+            "tsdf_block_key", "tsdf_block_slot", "tsdf_status_string", "tsdf_version",
+            "tsdf_launch_count")
+
+
+class tsdf_intrinsics(ctypes.Structure):
+    _fields_ = [("fx", ctypes.c_float), ("fy", ctypes.c_float), ("cx", ctypes.c_float),
+                ("cy", ctypes.c_float)]
+
+
+class tsdf_pose(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_float * 16)]
+
+
+class tsdf_layout(ctypes.Structure):
+    _fields_ = [("base", ctypes.c_void_p), ("bytes", ctypes.c_size_t),
+                ("block_count", ctypes.c_void_p), ("error_word", ctypes.c_void_p),
+                ("table", ctypes.c_void_p), ("block_coords", ctypes.c_void_p),
+                ("channel", ctypes.c_void_p * 5), ("table_slots", ctypes.c_uint32),
+                ("pool_blocks", ctypes.c_uint32), ("table_offset", ctypes.c_size_t),
+                ("coords_offset", ctypes.c_size_t), ("channel_offset", ctypes.c_size_t * 5)]
+
+
+class TsdfError(RuntimeError):
+    def __init__(self, status: str, where: str = ""):
+        super().__init__(f"{where}: TSDF_ERR_{status}" if where else f"TSDF_ERR_{status}")
+        self.status = status
+
+
+_lib = None
+_P = ctypes.c_void_p
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libtsdf.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise RuntimeError(
+                f"libtsdf.so is not built ({LIB}); run "
+                "`python -c 'import __graft_entry__ as g; g.build()'` first")
+        L = ctypes.CDLL(LIB)
+        st = ctypes.c_int
+        sig = {
+            "tsdf_volume_bytes": (ctypes.c_size_t, [ctypes.c_uint32, ctypes.c_uint32]),
+            "tsdf_volume_create": (st, [ctypes.c_float, ctypes.c_float, ctypes.c_uint32,
+                                        ctypes.c_uint32, ctypes.POINTER(_P)]),
+            "tsdf_volume_create_in": (st, [_P, ctypes.c_size_t, ctypes.c_float, ctypes.c_float,
+                                           ctypes.c_uint32, ctypes.c_uint32, _P,
+                                           ctypes.POINTER(_P)]),
+            "tsdf_volume_reset": (st, [_P, _P]),
+            "tsdf_volume_destroy": (None, [_P]),
+            "tsdf_volume_set_option": (st, [_P, ctypes.c_int, ctypes.c_int64]),
+            "tsdf_volume_layout": (st, [_P, ctypes.POINTER(tsdf_layout)]),
+            "tsdf_fuse_frame": (st, [_P, _P, ctypes.c_int, ctypes.c_int,
+                                     ctypes.POINTER(tsdf_intrinsics), ctypes.POINTER(tsdf_pose),
+                                     _P, _P]),
+            "tsdf_fuse_frame_async": (st, [_P, _P, ctypes.c_int, ctypes.c_int,
+                                           ctypes.POINTER(tsdf_intrinsics),
+                                           ctypes.POINTER(tsdf_pose), _P, _P]),
+            "tsdf_fuse_frame_host": (st, [_P, _P, ctypes.c_int, ctypes.c_int,
+                                          ctypes.POINTER(tsdf_intrinsics),
+                                          ctypes.POINTER(tsdf_pose), _P, _P]),
+            "tsdf_allocate_async": (st, [_P, _P, ctypes.c_int, ctypes.c_int,
+                                         ctypes.POINTER(tsdf_intrinsics),
+                                         ctypes.POINTER(tsdf_pose), _P]),
+            "tsdf_integrate_async": (st, [_P, _P, ctypes.c_int, ctypes.c_int,
+                                          ctypes.POINTER(tsdf_intrinsics),
+                                          ctypes.POINTER(tsdf_pose), _P, _P]),
+            "tsdf_volume_status": (st, [_P, _P]),
+            "tsdf_volume_block_count": (st, [_P, _P, ctypes.POINTER(ctypes.c_uint32)]),
+            "tsdf_export_blocks": (st, [_P, _P, _P, ctypes.c_uint32,
+                                        ctypes.POINTER(ctypes.c_uint32), _P]),
+            "tsdf_block_key": (ctypes.c_uint64, [ctypes.c_int32] * 3),
+            "tsdf_block_slot": (ctypes.c_uint32, [ctypes.c_int32] * 3 + [ctypes.c_uint32]),
+            "tsdf_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+            "tsdf_version": (ctypes.c_char_p, []),
+            "tsdf_launch_count": (ctypes.c_uint64, []),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+# ----------------------------------------------------------------------------
+# marshalling helpers
+# ----------------------------------------------------------------------------
+def _dptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if hasattr(x, "is_cuda") and not x.is_cuda:
+            raise ValueError("expected a CUDA tensor")
+        if hasattr(x, "is_contiguous") and not x.is_contiguous():
+            raise ValueError("expected a contiguous tensor")
+        return x.data_ptr()
+    raise TypeError(f"cannot take a device address of {type(x)}")
+
+
+def _hptr(x):
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if not x.flags.c_contiguous:
+            raise ValueError("expected a C-contiguous array")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if getattr(x, "is_cuda", False):
+            raise ValueError("expected a host tensor")
+        return x.data_ptr()
+    if isinstance(x, int):
+        return x
+    raise TypeError(f"cannot take a host address of {type(x)}")
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s or None
+    return getattr(s, "cuda_stream", 0) or None
+
+
+def _intr(intr):
+    a = [float(x) for x in np.asarray(intr, dtype=np.float32).reshape(4)]
+    return ctypes.byref(tsdf_intrinsics(*a))
+
+
+def _pose(pose):
+    p = tsdf_pose()
+    for i, x in enumerate(np.asarray(pose, dtype=np.float32).reshape(16)):
+        p.m[i] = float(x)
+    return ctypes.byref(p)
+
+
+def _st(code: int) -> str:
+    return STATUS.get(int(code), f"UNKNOWN({code})")
+
+
+# ----------------------------------------------------------------------------
+# the C entry points
+# ----------------------------------------------------------------------------
+def tsdf_volume_bytes(table_slots: int, pool_blocks: int) -> int:
+    return int(lib().tsdf_volume_bytes(table_slots, pool_blocks))
+
+
+def tsdf_volume_create(voxel_size, truncation, table_slots, pool_blocks):
+    h = _P()
+    st = _st(lib().tsdf_volume_create(voxel_size, truncation, table_slots, pool_blocks,
+                                      ctypes.byref(h)))
+    if st != "OK":
+        raise TsdfError(st, "tsdf_volume_create")
+    return h
+
+
+def tsdf_volume_create_in(dev_mem, nbytes, voxel_size, truncation, table_slots, pool_blocks,
+                          stream=None):
+    h = _P()
+    st = _st(lib().tsdf_volume_create_in(_dptr(dev_mem), nbytes, voxel_size, truncation,
+                                         table_slots, pool_blocks, _stream(stream),
+                                         ctypes.byref(h)))
+    if st != "OK":
+        raise TsdfError(st, "tsdf_volume_create_in")
+    return h
+
+
+def tsdf_volume_reset(vol, stream=None) -> str:
+    return _st(lib().tsdf_volume_reset(vol, _stream(stream)))
+
+
+def tsdf_volume_destroy(vol) -> None:
+    lib().tsdf_volume_destroy(vol)
+
+
+def tsdf_volume_set_option(vol, option, value) -> str:
+    opt = OPTIONS[option] if isinstance(option, str) else int(option)
+    return _st(lib().tsdf_volume_set_option(vol, opt, int(value)))
+
+
+def tsdf_volume_layout(vol) -> tsdf_layout:
+    out = tsdf_layout()
+    st = _st(lib().tsdf_volume_layout(vol, ctypes.byref(out)))
+    if st != "OK":
+        raise TsdfError(st, "tsdf_volume_layout")
+    return out
+
+
+def tsdf_fuse_frame(vol, depth, width, height, intr, pose, rgb=None, stream=None) -> str:
+    return _st(lib().tsdf_fuse_frame(vol, _dptr(depth), width, height, _intr(intr), _pose(pose),
+                                     _dptr(rgb), _stream(stream)))
+
+
+def tsdf_fuse_frame_async(vol, depth, width, height, intr, pose, rgb=None, stream=None) -> str:
+    return _st(lib().tsdf_fuse_frame_async(vol, _dptr(depth), width, height, _intr(intr),
+                                           _pose(pose), _dptr(rgb), _stream(stream)))
+
+
+def tsdf_fuse_frame_host(vol, depth, width, height, intr, pose, rgb=None, stream=None) -> str:
+    return _st(lib().tsdf_fuse_frame_host(vol, _hptr(depth), width, height, _intr(intr),
+                                          _pose(pose), _hptr(rgb), _stream(stream)))
+
+
+def tsdf_allocate_async(vol, depth, width, height, intr, pose, stream=None) -> str:
+    return _st(lib().tsdf_allocate_async(vol, _dptr(depth), width, height, _intr(intr),
+                                         _pose(pose), _stream(stream)))
+
+
+def tsdf_integrate_async(vol, depth, width, height, intr, pose, rgb=None, stream=None) -> str:
+    return _st(lib().tsdf_integrate_async(vol, _dptr(depth), width, height, _intr(intr),
+                                          _pose(pose), _dptr(rgb), _stream(stream)))
+
+
+def tsdf_volume_status(vol, stream=None) -> str:
+    return _st(lib().tsdf_volume_status(vol, _stream(stream)))
+
+
+def tsdf_volume_block_count(vol, stream=None) -> int:
+    n = ctypes.c_uint32()
+    st = _st(lib().tsdf_volume_block_count(vol, _stream(stream), ctypes.byref(n)))
+    if st != "OK":
+        raise TsdfError(st, "tsdf_volume_block_count")
+    return int(n.value)
+
+
+def tsdf_export_blocks(vol, stream=None):
+    """(coords int32 (n,3), voxels float32 (n,5,512)) in pool order."""
+    n = ctypes.c_uint32()
+    st = _st(lib().tsdf_export_blocks(vol, None, None, 0, ctypes.byref(n), _stream(stream)))
+    if st != "OK":
+        raise TsdfError(st, "tsdf_export_blocks")
+    coords = np.zeros((n.value, 3), dtype=np.int32)
+    vox = np.zeros((n.value, 5, 512), dtype=np.float32)
+    if n.value:
+        m = ctypes.c_uint32()
+        st = _st(lib().tsdf_export_blocks(vol, coords.ctypes.data, vox.ctypes.data, n.value,
+                                          ctypes.byref(m), _stream(stream)))
+        if st != "OK":
+            raise TsdfError(st, "tsdf_export_blocks")
+    return coords, vox
+
+
+def tsdf_block_key(bx, by, bz) -> int:
+    return int(lib().tsdf_block_key(bx, by, bz))
+
+
+def tsdf_block_slot(bx, by, bz, table_slots) -> int:
+    return int(lib().tsdf_block_slot(bx, by, bz, table_slots))
+
+
+def tsdf_status_string(code: int) -> str:
+    return lib().tsdf_status_string(code).decode()
+
+
+def tsdf_version() -> str:
+    return lib().tsdf_version().decode()
+
+
+def tsdf_launch_count() -> int:
+    return int(lib().tsdf_launch_count())
+
+
+# ----------------------------------------------------------------------------
+# convenience: an owning handle
+# ----------------------------------------------------------------------------
+class Volume:
+    """Owning wrapper around a tsdf_volume*; every method is one C call."""
+
+    def __init__(self, voxel_size, truncation, table_slots, pool_blocks, memory=None,
+                 stream=None):
+        self.voxel_size = float(voxel_size)
+        self.truncation = float(truncation)
+        self.table_slots = int(table_slots)
+        self.pool_blocks = int(pool_blocks)
+        self._memory = memory
+        if memory is None:
+            self.handle = tsdf_volume_create(voxel_size, truncation, table_slots, pool_blocks)
+        else:
+            nbytes = memory.numel() * memory.element_size()
+            self.handle = tsdf_volume_create_in(memory, nbytes, voxel_size, truncation,
+                                                table_slots, pool_blocks, stream)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            tsdf_volume_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def fuse(self, depth, intr, pose, rgb=None, stream=None, sync=True) -> str:
+        h, w = depth.shape[-2], depth.shape[-1]
+        fn = tsdf_fuse_frame if sync else tsdf_fuse_frame_async
+        return fn(self.handle, depth, w, h, intr, pose, rgb, stream)
+
+    def fuse_host(self, depth, intr, pose, rgb=None, stream=None) -> str:
+        h, w = depth.shape[-2], depth.shape[-1]
+        return tsdf_fuse_frame_host(self.handle, depth, w, h, intr, pose, rgb, stream)
+
+    def status(self, stream=None) -> str:
+        return tsdf_volume_status(self.handle, stream)
+
+    def reset(self, stream=None) -> str:
+        return tsdf_volume_reset(self.handle, stream)
+
+    def block_count(self, stream=None) -> int:
+        return tsdf_volume_block_count(self.handle, stream)
+
+    def export(self, stream=None):
+        return tsdf_export_blocks(self.handle, stream)
+
+    def set_option(self, option, value) -> str:
+        return tsdf_volume_set_option(self.handle, option, value)
+
+    def layout(self) -> tsdf_layout:
+        return tsdf_volume_layout(self.handle)

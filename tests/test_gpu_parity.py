@@ -1,0 +1,309 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Acceptance (paper Section 3.3 "Correctness": same block count, no dropped
+points; means recovered from sums, Section 2.2):
+  * the allocated block-key set is identical (compared as a set: slot and pool
+    order are free);
+  * the integer-valued weights are identical;
+  * tsdf and colour means agree within 1e-5 absolute (float32 sums in a
+    different order against the oracle's double sums; weights per voxel stay
+    far below the 1e3 contributions at which float32 order error could reach
+    1e-5 for values bounded by 1);
+  * the status codes are identical.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+from paper_2608_08287_gb300 import synth, tsdf
+from voxels import sort_blocks
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2608_08287_gb300.build import build_library
+    build_library()
+    oracle.build()
+    torch.cuda.set_device(0)
+
+
+def to_dev(frame, with_rgb=True):
+    d = torch.from_numpy(np.ascontiguousarray(frame.depth)).cuda()
+    c = torch.from_numpy(np.ascontiguousarray(frame.rgb)).cuda() if with_rgb else None
+    return d, c
+
+
+def gpu_volume(spec, **opts):
+    v = tsdf.Volume(spec.voxel_size, spec.truncation, spec.table_slots, spec.pool_blocks)
+    for k, x in opts.items():
+        assert v.set_option(k, x) == "OK"
+    return v
+
+
+def oracle_volume(spec):
+    return oracle.OracleVolume(spec.voxel_size, spec.truncation, spec.table_slots,
+                               spec.pool_blocks)
+
+
+def assert_same_volume(gv, ov, with_rgb=True):
+    gc, gx = sort_blocks(*gv.export())
+    oc, ox = ov.export(double=True)
+    assert gc.shape == oc.shape, (gc.shape, oc.shape)
+    assert np.array_equal(gc, oc), "block-key sets differ"
+    assert np.array_equal(gx[:, 1], ox[:, 1].astype(np.float32)), "weights differ"
+    err_t = float(np.max(np.abs(gx[:, 0] - ox[:, 0]))) if len(gc) else 0.0
+    assert err_t <= TOL, err_t
+    if with_rgb:
+        err_c = float(np.max(np.abs(gx[:, 2:] - ox[:, 2:]))) if len(gc) else 0.0
+        assert err_c <= TOL, err_c
+    else:
+        assert not np.any(gx[:, 2:])
+    assert gv.block_count() == ov.block_count()
+    return len(gc)
+
+
+def fuse_both(frames, spec, with_rgb=True, **opts):
+    gv = gpu_volume(spec, **opts)
+    ov = oracle_volume(spec)
+    for f in frames:
+        d, c = to_dev(f, with_rgb)
+        sg = gv.fuse(d, f.intr, f.pose, c)
+        so = ov.fuse_frame(f, with_rgb=with_rgb)
+        assert sg == so, (sg, so)
+    return gv, ov
+
+
+# ----------------------------------------------------------------------------
+# the workloads
+# ----------------------------------------------------------------------------
+def test_plane_sphere_160x120():
+    gv, ov = fuse_both([synth.plane_sphere_frame()], synth.PLANE_SPHERE_160)
+    n = assert_same_volume(gv, ov)
+    assert n == ov.last_stats["unique_blocks"] > 500
+
+
+def test_room_640x480_full_frame():
+    """The benchmark's workload, in the launch configuration it times."""
+    gv, ov = fuse_both([synth.room_frame(0)], synth.ROOM_640)
+    n = assert_same_volume(gv, ov)
+    assert n == ov.last_stats["unique_blocks"] > 5000
+
+
+@pytest.mark.parametrize("seed", range(64))
+def test_random_tiny_frames(seed):
+    f = synth.random_frame(2000 + seed, width=16 + seed % 5, height=12 + seed % 3)
+    v, tau = [(0.05, 0.2), (0.1, 0.3), (0.03, 0.12), (0.02, 0.1)][seed % 4]
+    spec = synth.VolumeSpec(v, tau, 1 << 12, 1 << 12)
+    gv, ov = fuse_both([f], spec)
+    assert_same_volume(gv, ov)
+
+
+def test_ragged_tiles_and_odd_sizes():
+    """Image sizes that are not multiples of the 16x16 tile, down to 1x1."""
+    for (w, h) in [(1, 1), (17, 3), (33, 31), (100, 7), (161, 121)]:
+        f = synth.room_frame(5, width=w, height=h)
+        spec = synth.VolumeSpec(0.02, 0.08, 1 << 14, 1 << 12)
+        gv, ov = fuse_both([f], spec)
+        assert_same_volume(gv, ov)
+
+
+def test_multi_frame_accumulation():
+    frames = [synth.room_frame(i * 7, width=160, height=120) for i in range(8)]
+    gv, ov = fuse_both(frames, synth.VolumeSpec(0.01, 0.04, 1 << 16, 1 << 14))
+    assert_same_volume(gv, ov)
+
+
+def test_without_colour():
+    gv, ov = fuse_both([synth.plane_sphere_frame()], synth.PLANE_SPHERE_160, with_rgb=False)
+    assert_same_volume(gv, ov, with_rgb=False)
+
+
+def test_empty_and_invalid_frames():
+    spec = synth.VolumeSpec(0.01, 0.04, 1 << 10, 1 << 8)
+    zero = synth.Frame(depth=np.zeros((24, 32), np.float32), rgb=np.zeros((24, 32, 3), np.uint8),
+                       intr=np.array([30, 30, 16, 12], np.float32), pose=np.eye(4, dtype=np.float32))
+    nan = synth.Frame(depth=np.full((24, 32), np.nan, np.float32), rgb=zero.rgb, intr=zero.intr,
+                      pose=zero.pose)
+    gv, ov = fuse_both([zero, nan], spec)
+    assert assert_same_volume(gv, ov) == 0
+
+
+# ----------------------------------------------------------------------------
+# variants must not change the result
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("policy", [0, 1, 2])
+def test_probe_load_policies(policy):
+    gv, ov = fuse_both([synth.room_frame(3, width=320, height=240)],
+                       synth.VolumeSpec(0.005, 0.02, 1 << 16, 1 << 15), probe_load=policy)
+    assert_same_volume(gv, ov)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_integrate_modes(mode):
+    gv, ov = fuse_both([synth.room_frame(40)], synth.ROOM_640, integrate_mode=mode)
+    assert_same_volume(gv, ov)
+
+
+def test_stage_split_and_async_match_sync():
+    f = synth.room_frame(11, width=320, height=240)
+    spec = synth.VolumeSpec(0.005, 0.02, 1 << 16, 1 << 15)
+    d, c = to_dev(f)
+    a = gpu_volume(spec)
+    assert tsdf.tsdf_allocate_async(a.handle, d, f.width, f.height, f.intr, f.pose) == "OK"
+    assert tsdf.tsdf_integrate_async(a.handle, d, f.width, f.height, f.intr, f.pose, c) == "OK"
+    assert a.status() == "OK"
+    b = gpu_volume(spec)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        assert b.fuse(d, f.intr, f.pose, c, stream=s, sync=False) == "OK"
+    assert b.status(stream=s) == "OK"
+    h = gpu_volume(spec)
+    depth_h = torch.from_numpy(f.depth).pin_memory()
+    rgb_h = torch.from_numpy(f.rgb).pin_memory()
+    assert h.fuse_host(depth_h, f.intr, f.pose, rgb_h) == "OK"
+    ov = oracle_volume(spec)
+    ov.fuse_frame(f)
+    for v in (a, b, h):
+        assert_same_volume(v, ov)
+
+
+def test_volume_in_caller_memory_and_reset():
+    spec = synth.PLANE_SPHERE_160
+    nbytes = tsdf.tsdf_volume_bytes(spec.table_slots, spec.pool_blocks)
+    mem = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    gv = tsdf.Volume(spec.voxel_size, spec.truncation, spec.table_slots, spec.pool_blocks,
+                     memory=mem)
+    f1, f2 = synth.plane_sphere_frame(seed=5), synth.plane_sphere_frame(seed=6)
+    d1, c1 = to_dev(f1)
+    d2, c2 = to_dev(f2)
+    assert gv.fuse(d1, f1.intr, f1.pose, c1) == "OK"
+    assert gv.reset() == "OK"
+    assert gv.block_count() == 0
+    assert gv.fuse(d2, f2.intr, f2.pose, c2) == "OK"
+    ov = oracle_volume(spec)
+    ov.fuse_frame(f2)
+    assert_same_volume(gv, ov)
+    lay = gv.layout()
+    assert lay.base == mem.data_ptr() and lay.bytes == nbytes
+
+
+# ----------------------------------------------------------------------------
+# load and overflow (Section 7.2: never lose a block silently)
+# ----------------------------------------------------------------------------
+def high_load_frames(slots, target=0.93, v=0.01, width=160, height=120, step=3):
+    """Orbit frames whose union of blocks fills `slots` to at least `target` load
+    without exceeding it (counted with the oracle)."""
+    probe = oracle_volume(synth.VolumeSpec(v, 4 * v, 1 << 22, 1 << 22))
+    frames = []
+    for i in range(0, 300, step):
+        f = synth.room_frame(i, width=width, height=height)
+        probe.fuse_frame(f)
+        if probe.block_count() > slots:
+            break
+        frames.append(f)
+        if probe.block_count() >= target * slots:
+            break
+    return frames
+
+
+def test_high_load_factor_zero_lost_blocks():
+    """Table and pool sized so the final load factor exceeds 0.9: the unbounded
+    probe keeps every block (the bounded probe of Section 7.2 loses blocks from a
+    load of 0.071 on)."""
+    slots = 1 << 12
+    frames = high_load_frames(slots)
+    spec = synth.VolumeSpec(0.01, 0.04, slots, slots)
+    gv, ov = fuse_both(frames, spec)
+    n = assert_same_volume(gv, ov)
+    assert n / slots > 0.9, n / slots
+
+
+@pytest.mark.parametrize("pool", [1, 4, 16, "D-1"])
+def test_pool_overflow_reported(pool):
+    f = synth.plane_sphere_frame()
+    spec = synth.PLANE_SPHERE_160
+    D = fuse_both([f], spec)[1].block_count()
+    p = D - 1 if pool == "D-1" else pool
+    small = synth.VolumeSpec(spec.voxel_size, spec.truncation, spec.table_slots, p)
+    gv = gpu_volume(small)
+    d, c = to_dev(f)
+    assert gv.fuse(d, f.intr, f.pose, c) == "POOL_FULL"
+    assert gv.block_count() == p
+    assert gv.fuse(d, f.intr, f.pose, c) == "POISONED"
+    assert gv.reset() == "OK"
+    big = gpu_volume(spec)
+    assert big.fuse(d, f.intr, f.pose, c) == "OK"
+
+
+def test_table_overflow_reported():
+    f = synth.plane_sphere_frame()
+    spec = synth.VolumeSpec(0.01, 0.04, 64, 64)
+    gv = gpu_volume(spec)
+    ov = oracle_volume(spec)
+    d, c = to_dev(f)
+    assert ov.fuse_frame(f) == "TABLE_FULL"
+    assert gv.fuse(d, f.intr, f.pose, c) == "TABLE_FULL"
+    assert gv.block_count() == 64
+
+
+def test_publish_timeout_is_bounded():
+    """An entry whose key matches a block the frame needs but whose index is never
+    published (Section 2.3, the publication window). The waiters give up after
+    the configured limit and the call returns an error; the GPU stays usable."""
+    f = synth.plane_sphere_frame()
+    spec = synth.PLANE_SPHERE_160
+    ov = oracle_volume(spec)
+    ov.fuse_frame(f)
+    coords, _ = ov.export()
+    bx, by, bz = (int(x) for x in coords[len(coords) // 2])
+    nbytes = tsdf.tsdf_volume_bytes(spec.table_slots, spec.pool_blocks)
+    mem = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    gv = tsdf.Volume(spec.voxel_size, spec.truncation, spec.table_slots, spec.pool_blocks,
+                     memory=mem)
+    assert gv.set_option("publish_timeout_ns", 20_000_000) == "OK"
+    torch.cuda.synchronize()
+    lay = gv.layout()
+    slot = tsdf.tsdf_block_slot(bx, by, bz, spec.table_slots)
+    key = tsdf.tsdf_block_key(bx, by, bz)
+    ent = np.zeros(2, dtype=np.uint64)
+    ent[0] = np.uint64(key)
+    ent[1] = np.uint64(0x00000000FFFFFFFF)  # idx = -1 (unpublished), pad = 0
+    off = lay.table_offset + 16 * slot
+    mem[off:off + 16].copy_(torch.from_numpy(ent.view(np.uint8)))
+    d, c = to_dev(f)
+    assert gv.fuse(d, f.intr, f.pose, c) == "PUBLISH_TIMEOUT"
+    assert gv.fuse(d, f.intr, f.pose, c) == "POISONED"
+    assert gv.reset() == "OK"
+    assert gv.fuse(d, f.intr, f.pose, c) == "OK"
+    assert_same_volume(gv, ov)
+
+
+def test_block_coordinates_match_table():
+    """Every published index points at a coordinate row that matches its key."""
+    f = synth.room_frame(2, width=320, height=240)
+    spec = synth.VolumeSpec(0.005, 0.02, 1 << 16, 1 << 15)
+    nbytes = tsdf.tsdf_volume_bytes(spec.table_slots, spec.pool_blocks)
+    mem = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    gv = tsdf.Volume(spec.voxel_size, spec.truncation, spec.table_slots, spec.pool_blocks,
+                     memory=mem)
+    d, c = to_dev(f)
+    assert gv.fuse(d, f.intr, f.pose, c) == "OK"
+    lay = gv.layout()
+    table = mem[lay.table_offset:lay.table_offset + 16 * spec.table_slots].cpu().numpy()
+    table = table.view(np.uint64).reshape(-1, 2)
+    used = table[:, 0] != np.uint64(tsdf.EMPTY_KEY)
+    idx = (table[used, 1] & np.uint64(0xFFFFFFFF)).astype(np.int64)
+    n = gv.block_count()
+    assert used.sum() == n and sorted(idx.tolist()) == list(range(n))
+    coords = mem[lay.coords_offset:lay.coords_offset + 12 * n].cpu().numpy().view(np.int32)
+    coords = coords.reshape(-1, 3)
+    for key, i in zip(table[used, 0].tolist(), idx.tolist()):
+        assert tsdf.tsdf_block_key(*(int(x) for x in coords[i])) == key

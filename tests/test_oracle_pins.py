@@ -259,8 +259,11 @@ def test_overflow_reported_and_poisons():
     assert bad.fuse_frame(f) == "POISONED"
     bad.reset()
     assert bad.block_count() == 0
-    tiny, st = _fuse(f, spec.voxel_size, spec.truncation, slots=16, pool=16)
+    tiny, st = _fuse(f, spec.voxel_size, spec.truncation, slots=64, pool=16)
     assert st == "POOL_FULL" and tiny.block_count() == 16
+    # with the pool as large as the table, the table is what runs out
+    full, st = _fuse(f, spec.voxel_size, spec.truncation, slots=16, pool=16)
+    assert st == "TABLE_FULL" and full.block_count() == 16
 
 
 def test_rejects_bad_parameters():
