@@ -188,6 +188,30 @@ tsdf_status tsdf_fuse_frame_host(tsdf_volume* vol, const float* depth_host, int 
                                  const tsdf_pose* pose, const uint8_t* rgb_host,
                                  void* stream);
 
+/* Largest frame (width * height) tsdf_fuse_frame_host_noalloc accepts. */
+#define TSDF_NOALLOC_MAX_PIXELS (1u << 20)
+
+/* As tsdf_fuse_frame_host, but allocates nothing. (The paper has no
+ * counterpart; this is for callers of this library.) Callers that cannot let
+ * the library call cudaMalloc -- a real-time loop that must not stall on an
+ * allocation, a process whose device memory is fully budgeted by its own
+ * allocator, a plugin host that forbids plugins to own device memory -- use
+ * this call: the frame is staged in one fixed array compiled into the library
+ * (TSDF_NOALLOC_MAX_PIXELS * 7 bytes, 7 MiB, held by every GPU that loads the
+ * library until the process exits) instead of volume-owned staging.
+ * width * height above TSDF_NOALLOC_MAX_PIXELS returns TSDF_ERR_INVALID_ARG
+ * and does nothing. The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress, with that device current); make that first
+ * call before any stream capture. Every call on a device shares the one array:
+ * calls whose work overlaps on the GPU (two host threads, or two streams)
+ * race on it and must be serialised by the caller. Each call waits for
+ * `stream` before returning, so consecutive calls from one thread are safe.
+ * The array keeps the last frame; each call overwrites what it reads. */
+tsdf_status tsdf_fuse_frame_host_noalloc(tsdf_volume* vol, const float* depth_host, int width,
+                                         int height, const tsdf_intrinsics* intr,
+                                         const tsdf_pose* pose, const uint8_t* rgb_host,
+                                         void* stream);
+
 /* Stage A alone (Section 2.2 "Allocate"): enqueue block allocation. */
 tsdf_status tsdf_allocate_async(tsdf_volume* vol, const float* depth_dev, int width,
                                 int height, const tsdf_intrinsics* intr,

@@ -23,12 +23,14 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OUT_OF_MEMORY", 3: "POOL_FULL", 4: "TAB
 OPTIONS = {"probe_load": 0, "publish_timeout_ns": 1, "integrate_mode": 2, "threads": 3}
 ERRBITS = {"POOL_FULL": 1, "TABLE_FULL": 2, "PUBLISH_TIMEOUT": 4, "BOUNDS": 8}
 EMPTY_KEY = 0xFFFFFFFFFFFFFFFF
+NOALLOC_MAX_PIXELS = 1 << 20
 CHANNELS = ("tsdf", "weight", "r", "g", "b")
 
 EXPORTED = ("tsdf_volume_bytes", "tsdf_volume_create", "tsdf_volume_create_in",
             "tsdf_volume_reset", "tsdf_volume_destroy", "tsdf_volume_set_option",
             "tsdf_volume_layout", "tsdf_fuse_frame", "tsdf_fuse_frame_async",
-            "tsdf_fuse_frame_host", "tsdf_allocate_async", "tsdf_integrate_async",
+            "tsdf_fuse_frame_host", "tsdf_fuse_frame_host_noalloc", "tsdf_allocate_async",
+            "tsdf_integrate_async",
             "tsdf_volume_status", "tsdf_volume_block_count", "tsdf_export_blocks",
             "tsdf_block_key", "tsdf_block_slot", "tsdf_status_string", "tsdf_version",
             "tsdf_launch_count")
@@ -92,6 +94,9 @@ def lib() -> ctypes.CDLL:
             "tsdf_fuse_frame_host": (st, [_P, _P, ctypes.c_int, ctypes.c_int,
                                           ctypes.POINTER(tsdf_intrinsics),
                                           ctypes.POINTER(tsdf_pose), _P, _P]),
+            "tsdf_fuse_frame_host_noalloc": (st, [_P, _P, ctypes.c_int, ctypes.c_int,
+                                                  ctypes.POINTER(tsdf_intrinsics),
+                                                  ctypes.POINTER(tsdf_pose), _P, _P]),
             "tsdf_allocate_async": (st, [_P, _P, ctypes.c_int, ctypes.c_int,
                                          ctypes.POINTER(tsdf_intrinsics),
                                          ctypes.POINTER(tsdf_pose), _P]),
@@ -234,6 +239,15 @@ def tsdf_fuse_frame_async(vol, depth, width, height, intr, pose, rgb=None, strea
 def tsdf_fuse_frame_host(vol, depth, width, height, intr, pose, rgb=None, stream=None) -> str:
     return _st(lib().tsdf_fuse_frame_host(vol, _hptr(depth), width, height, _intr(intr),
                                           _pose(pose), _hptr(rgb), _stream(stream)))
+
+
+def tsdf_fuse_frame_host_noalloc(vol, depth, width, height, intr, pose, rgb=None,
+                                 stream=None) -> str:
+    """Host-input fusion that allocates nothing: the frame is staged in a fixed
+    array inside the library (at most NOALLOC_MAX_PIXELS pixels), for callers
+    that cannot let the library call cudaMalloc."""
+    return _st(lib().tsdf_fuse_frame_host_noalloc(vol, _hptr(depth), width, height, _intr(intr),
+                                                  _pose(pose), _hptr(rgb), _stream(stream)))
 
 
 def tsdf_allocate_async(vol, depth, width, height, intr, pose, stream=None) -> str:
