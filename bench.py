@@ -3,12 +3,14 @@
 640x480 synthetic room frame into a hash-blocked TSDF volume (voxel 5 mm,
 truncation 2 cm, 2^20 table slots, 2^18 pool blocks).
 
-One step = one pass of the whole hot path (stage A allocate + stage B
-integrate, paper Section 2.2) over one frame, into a freshly reset volume (so
-stage A never degenerates into a lookup-only pass, Section 4.2). Between steps,
-outside the timed events, the volume is reset and L2 is flushed by a 512 MB
-write. Each step is timed with CUDA events on the launching stream; stage A
-and stage B also have their own events.
+One step = one pass of the whole hot path (allocate + integrate, paper
+Section 2.2) over one frame through tsdf_fuse_frame_async, into a freshly
+reset volume (so allocation never degenerates into a lookup-only pass,
+Section 4.2). Between steps, outside the timed events, the volume is reset and
+L2 is scrubbed (512 MB write, then 512 MB read). Each step is timed with CUDA
+events on the launching stream. The same frames are also run as the two
+separate stages (stage A, then stage B), each with its own events, for the
+per-stage rooflines.
 
 Prints ONE JSON line. With --impl reference the CPU oracle (single thread,
 host cores) is timed on the same workload instead.
@@ -53,8 +55,17 @@ def config_dict(spec, frames):
             "table_slots": spec.table_slots, "pool_blocks": spec.pool_blocks,
             "points_per_frame": int(np.mean([f.valid_points for f in frames])),
             "distinct_frames": len(frames), "colour": True,
-            "l2": "flushed between steps (512 MB write outside the timed events)",
+            "l2": "flushed between steps (512 MB write + 512 MB read, outside the timed events)",
             "volume": "reset between steps: every step fuses into an empty volume"}
+
+
+def l2_scrub(flush, scrub, i):
+    """Leave L2 cold and clean: write 512 MB (evicts everything), then read
+    another 512 MB (writes those dirty lines back and refills L2 with clean
+    lines), so the timed kernels neither hit in L2 nor pay for write-backs of
+    the scrub."""
+    flush.fill_(i & 0xFF)
+    scrub.sum()
 
 
 def make_frames(rank=0):
@@ -144,6 +155,10 @@ def committed_traffic(kernel):
 # ----------------------------------------------------------------------------
 # the GPU arm
 # ----------------------------------------------------------------------------
+def vol_fuse_mode(vol):
+    return getattr(vol, "_fuse_mode", 0)
+
+
 def run_gpu(args, rank, world, local_rank):
     import torch
     from paper_2608_08287_gb300 import synth, tsdf
@@ -157,13 +172,16 @@ def run_gpu(args, rank, world, local_rank):
     spec = synth.ROOM_640
     frames = make_frames(rank)
     vol = tsdf.Volume(spec.voxel_size, spec.truncation, spec.table_slots, spec.pool_blocks)
-    for k, x in (("probe_load", args.probe_load), ("integrate_mode", args.integrate_mode)):
+    for k, x in (("probe_load", args.probe_load), ("integrate_mode", args.integrate_mode),
+                 ("allocate_mode", args.allocate_mode), ("fuse_mode", args.fuse_mode)):
         if x is not None:
             assert vol.set_option(k, x) == "OK"
+    vol._fuse_mode = 0 if args.fuse_mode is None else args.fuse_mode
     stream = torch.cuda.Stream()
     sp = stream.cuda_stream
     dev = [(torch.from_numpy(f.depth).cuda(), torch.from_numpy(f.rgb).cuda()) for f in frames]
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    scrub = torch.ones(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     W, H = 640, 480
 
     # per-frame work counts from the GPU result itself (fresh volume each time)
@@ -175,28 +193,40 @@ def run_gpu(args, rank, world, local_rank):
         work.append({"points": f.valid_points, "blocks": len(coords),
                      "voxels": int((vox[:, 1] > 0).sum())})
 
-    def one_step(i, evs=None):
-        f = frames[i % len(frames)]
-        d, c = dev[i % len(frames)]
+    def prepare(i):
         vol.reset(sp)
         with torch.cuda.stream(stream):
-            flush.fill_(i & 0xFF)
+            l2_scrub(flush, scrub, i)
+
+    def one_step(i, evs=None):
+        """The whole hot path for one frame: tsdf_fuse_frame_async (default mode)."""
+        f = frames[i % len(frames)]
+        d, c = dev[i % len(frames)]
+        prepare(i)
         if evs:
             evs[0].record(stream)
-        assert tsdf.tsdf_allocate_async(vol.handle, d, W, H, f.intr, f.pose, sp) == "OK"
+        assert tsdf.tsdf_fuse_frame_async(vol.handle, d, W, H, f.intr, f.pose, c, sp) == "OK"
         if evs:
             evs[1].record(stream)
-        assert tsdf.tsdf_integrate_async(vol.handle, d, W, H, f.intr, f.pose, c, sp) == "OK"
-        if evs:
-            evs[2].record(stream)
         return f.valid_points
+
+    def split_step(i, evs):
+        """The same frame as two kernels, stage A then stage B, each timed."""
+        f = frames[i % len(frames)]
+        d, c = dev[i % len(frames)]
+        prepare(i)
+        evs[0].record(stream)
+        assert tsdf.tsdf_allocate_async(vol.handle, d, W, H, f.intr, f.pose, sp) == "OK"
+        evs[1].record(stream)
+        assert tsdf.tsdf_integrate_async(vol.handle, d, W, H, f.intr, f.pose, c, sp) == "OK"
+        evs[2].record(stream)
 
     for i in range(args.warmup):
         one_step(i)
     assert vol.status(sp) == "OK"
     torch.cuda.synchronize()
 
-    events = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    events = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -214,9 +244,7 @@ def run_gpu(args, rank, world, local_rank):
     launches = tsdf.tsdf_launch_count() - launches0
     st = vol.status(sp)
     assert st == "OK", st
-    ta = [events[i][0].elapsed_time(events[i][1]) for i in range(args.steps)]
-    tb_ = [events[i][1].elapsed_time(events[i][2]) for i in range(args.steps)]
-    step_ms = [a + b for a, b in zip(ta, tb_)]
+    step_ms = [events[i][0].elapsed_time(events[i][1]) for i in range(args.steps)]
     total_ms = float(sum(step_ms))
     if world > 1:
         t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
@@ -229,22 +257,42 @@ def run_gpu(args, rank, world, local_rank):
         points_all = points
     value = points_all / (total_ms / 1e3)
 
-    # roofline of the dominant stage (Section 8(d) algorithmic bytes)
+    # the two-stage split of the same frames, for the per-stage rooflines
+    n_split = min(args.steps, 100)
+    sev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(n_split)]
+    for i in range(3):
+        split_step(i, sev[0])
+    for i in range(n_split):
+        split_step(args.warmup + i, sev[i])
+    torch.cuda.synchronize()
+    assert vol.status(sp) == "OK"
+    ta = [e[0].elapsed_time(e[1]) for e in sev]
+    tb_ = [e[1].elapsed_time(e[2]) for e in sev]
+
+    # rooflines (Section 8(d) algorithmic bytes; work counts from the GPU's own export)
     hbm, peak_kind = peaks()
     mean = lambda k: float(np.mean([w[k] for w in work]))
     a_bytes = 4 * W * H + 16 * mean("blocks") + 28 * mean("blocks")
     b_bytes = 7 * W * H + 16 * mean("blocks") + 40 * mean("voxels")
+    f_bytes = 7 * W * H + 16 * mean("blocks") + 28 * mean("blocks") + 40 * mean("voxels")
     a_ms, b_ms = float(np.mean(ta)), float(np.mean(tb_))
+    step_mean = total_ms / args.steps
     a_gbs, b_gbs = a_bytes / (a_ms * 1e6), b_bytes / (b_ms * 1e6)
-    dom = ("integrate", b_bytes, b_ms, b_gbs) if b_ms >= a_ms else ("allocate", a_bytes, a_ms, a_gbs)
-    kname = {"integrate": "integrate_kernel", "allocate": "allocate_kernel"}[dom[0]]
+    f_gbs = f_bytes / (step_mean * 1e6)
+    fused = vol_fuse_mode(vol) == 1
+    if fused:
+        dom = ("fused", f_bytes, step_mean, f_gbs, "fuse_kernel")
+    elif b_ms >= a_ms:
+        dom = ("integrate", b_bytes, b_ms, b_gbs, "integrate_kernel")
+    else:
+        dom = ("allocate", a_bytes, a_ms, a_gbs, "allocate_kernel")
     roof = {"bound": "hbm", "kernel": dom[0], "achieved": round(dom[3], 1), "peak": hbm,
             "peak_kind": f"{peak_kind} hbm_gbs", "unit": "GB/s",
             "frac": round(dom[3] / hbm, 4), "algorithmic_bytes": int(dom[1]),
-            "traffic": committed_traffic(kname)}
+            "traffic": committed_traffic(dom[4])}
 
     # end to end through the public C ABI with host buffers
-    e2e = run_e2e(args, vol, frames, torch, tsdf, sp, stream, flush)
+    e2e = run_e2e(args, vol, frames, torch, tsdf, sp, stream, flush, scrub)
 
     out = None
     if rank == 0:
@@ -254,9 +302,12 @@ def run_gpu(args, rank, world, local_rank):
             "ms_per_step": round(total_ms / args.steps, 5), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": config_dict(spec, frames),
-            "stages": {"allocate_ms": round(a_ms, 5), "integrate_ms": round(b_ms, 5),
-                       "allocate_hbm_frac": round(a_gbs / hbm, 4),
-                       "integrate_hbm_frac": round(b_gbs / hbm, 4),
+            "stages": {"path": "fused kernel" if fused else "stage A + stage B",
+                       "fused_hbm_frac": round(f_gbs / hbm, 4),
+                       "split_allocate_ms": round(a_ms, 5), "split_integrate_ms": round(b_ms, 5),
+                       "split_allocate_hbm_frac": round(a_gbs / hbm, 4),
+                       "split_integrate_hbm_frac": round(b_gbs / hbm, 4),
+                       "split_pts_per_s": round(mean("points") / ((a_ms + b_ms) / 1e3), 1),
                        "step_ms_p50": round(float(np.percentile(step_ms, 50)), 5),
                        "step_ms_p95": round(float(np.percentile(step_ms, 95)), 5),
                        "step_ms_p99": round(float(np.percentile(step_ms, 99)), 5),
@@ -264,8 +315,8 @@ def run_gpu(args, rank, world, local_rank):
             "roofline": roof,
             "e2e": e2e,
             "gpu_launches": int(launches),
-            "gpu_launches_detail": "per step: 1 stage-A + 1 stage-B kernel (timed) + 1 reset "
-                                   "kernel (between steps, outside the step events)",
+            "gpu_launches_detail": "per step: the fusion kernel(s) inside the step events, plus "
+                                   "1 reset kernel between steps, outside them",
             "clocks": clk.summary(),
             "wall_s_timed_region": round(wall, 4),
             "kernel_source": kernel_source_hash(),
@@ -275,7 +326,7 @@ def run_gpu(args, rank, world, local_rank):
     return out
 
 
-def run_e2e(args, vol, frames, torch, tsdf, sp, stream, flush):
+def run_e2e(args, vol, frames, torch, tsdf, sp, stream, flush, scrub):
     """Same metric through tsdf_fuse_frame_host: pinned host depth + colour are
     copied in, both stages run, the status word is read back, every step."""
     host = [(torch.from_numpy(f.depth).pin_memory(), torch.from_numpy(f.rgb).pin_memory())
@@ -293,7 +344,7 @@ def run_e2e(args, vol, frames, torch, tsdf, sp, stream, flush):
         d, c = host[i % len(frames)]
         vol.reset(sp)
         with torch.cuda.stream(stream):
-            flush.fill_(i & 0xFF)
+            l2_scrub(flush, scrub, i)
         stream.synchronize()
         t0 = time.perf_counter()
         st = tsdf.tsdf_fuse_frame_host(vol.handle, d, W, H, f.intr, f.pose, c, sp)
@@ -366,11 +417,13 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--probe-load", type=int, default=None)
     ap.add_argument("--integrate-mode", type=int, default=None)
+    ap.add_argument("--allocate-mode", type=int, default=None)
+    ap.add_argument("--fuse-mode", type=int, default=None)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

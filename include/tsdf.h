@@ -64,7 +64,7 @@ typedef enum tsdf_status {
   TSDF_ERR_OUT_OF_MEMORY = 2,    /* a device or pinned allocation failed */
   TSDF_ERR_POOL_FULL = 3,        /* more blocks than pool_blocks (Section 3.4) */
   TSDF_ERR_TABLE_FULL = 4,       /* a probe scanned every slot without room */
-  TSDF_ERR_PUBLISH_TIMEOUT = 5,  /* a waiter gave up on an unpublished index */
+  TSDF_ERR_PUBLISH_TIMEOUT = 5,  /* a block index was never published */
   TSDF_ERR_BOUNDS = 6,           /* an index check failed (defensive) */
   TSDF_ERR_POISONED = 7,         /* volume holds an earlier error; reset it */
   TSDF_ERR_CUDA = 8              /* a CUDA runtime call failed */
@@ -92,7 +92,9 @@ typedef struct tsdf_layout {
   size_t table_offset, coords_offset, channel_offset[5]; /* byte offsets from base */
 } tsdf_layout;
 
-/* Sticky bits of the device error word. */
+/* Sticky bits of the device error word. PUBLISH_TIMEOUT is also set when
+ * stage B finds a block that was claimed but whose index was never
+ * published. */
 #define TSDF_ERRBIT_POOL_FULL 1u
 #define TSDF_ERRBIT_TABLE_FULL 2u
 #define TSDF_ERRBIT_PUBLISH_TIMEOUT 4u
@@ -112,12 +114,29 @@ typedef enum tsdf_option {
   /* Upper bound on the wait for a block index to be published, nanoseconds
    * (default 1e9). The wait gives up with TSDF_ERR_PUBLISH_TIMEOUT. */
   TSDF_OPT_PUBLISH_TIMEOUT_NS = 1,
-  /* Stage B strategy: 0 = one atomic add per contribution and channel (the
-   * paper's update stage), 1 = contributions aggregated per voxel in shared
-   * memory before one vector add per voxel group (default). */
+  /* Stage B strategy: 0 = each thread looks up its blocks in the table (a
+   * one-entry cache per point) and adds five sums per accepted voxel with
+   * fire-and-forget atomic additions, the paper's update stage (default);
+   * 1 = each warp dedupes its points' blocks with __match_any_sync and looks
+   * them up once, warp-cooperatively, then the same additions. */
   TSDF_OPT_INTEGRATE_MODE = 2,
-  /* Launch shape: threads per CTA for both stages (128, 256 or 512). */
-  TSDF_OPT_THREADS = 3
+  /* Launch shape: threads per CTA for both stages (256). */
+  TSDF_OPT_THREADS = 3,
+  /* Stage A strategy: 0 = the paper's protocol as printed (every warp-distinct
+   * key inserted as the walk finds it; a thread that finds its key waits for
+   * the index to be published); 1 = the distinct keys of each 16x16 pixel
+   * tile, via a shared-memory set, inserted warp-cooperatively after one
+   * barrier (default); 2 = the distinct keys of each warp inserted
+   * warp-cooperatively, no shared memory. In 1 and 2 counter increments are
+   * aggregated per warp and no thread waits: nothing in stage A consumes an
+   * index, and the kernel boundary publishes every index before stage B. */
+  TSDF_OPT_ALLOCATE_MODE = 4,
+  /* What tsdf_fuse_frame* launch: 0 = stage A then stage B (two kernels,
+   * Section 2.2, default); 1 = one fused kernel per frame in which each warp
+   * walks its points once, inserts its distinct blocks (waiting, bounded, for
+   * indices published by others) and adds its sums. Results are identical up
+   * to the order of floating-point additions. */
+  TSDF_OPT_FUSE_MODE = 5
 } tsdf_option;
 
 /* ---------------------------------------------------------------------------

@@ -63,7 +63,9 @@ struct tsdf_volume {
   bool poisoned = false;
   uint32_t* pinned = nullptr;  // {count, err}
   int probe_load = tsdf::kLoadCached;
-  int integrate_mode = 1;
+  int allocate_mode = 1;
+  int integrate_mode = 0;
+  int fuse_mode = 0;
   int threads = 256;
   void* stage = nullptr;
   size_t stage_bytes = 0;
@@ -281,6 +283,14 @@ tsdf_status tsdf_volume_set_option(tsdf_volume* vol, tsdf_option opt, int64_t va
       if (value != 256) return TSDF_ERR_INVALID_ARG;
       vol->threads = static_cast<int>(value);
       return TSDF_OK;
+    case TSDF_OPT_ALLOCATE_MODE:
+      if (value < 0 || value > 2) return TSDF_ERR_INVALID_ARG;
+      vol->allocate_mode = static_cast<int>(value);
+      return TSDF_OK;
+    case TSDF_OPT_FUSE_MODE:
+      if (value < 0 || value > 1) return TSDF_ERR_INVALID_ARG;
+      vol->fuse_mode = static_cast<int>(value);
+      return TSDF_OK;
   }
   return TSDF_ERR_INVALID_ARG;
 }
@@ -312,7 +322,7 @@ tsdf_status tsdf_allocate_async(tsdf_volume* vol, const float* depth_dev, int wi
   tsdf_status st = make_frame(vol, depth_dev, width, height, intr, pose, nullptr, &f);
   if (st != TSDF_OK) return st;
   if (vol->poisoned) return TSDF_ERR_POISONED;
-  return from_cuda(tsdf::launch_allocate(f, vol->va, vol->probe_load, as_stream(stream)));
+  return from_cuda(tsdf::launch_allocate(f, vol->va, vol->probe_load, vol->allocate_mode, as_stream(stream)));
 }
 
 tsdf_status tsdf_integrate_async(tsdf_volume* vol, const float* depth_dev, int width,
@@ -334,7 +344,11 @@ tsdf_status tsdf_fuse_frame_async(tsdf_volume* vol, const float* depth_dev, int 
   tsdf_status st = make_frame(vol, depth_dev, width, height, intr, pose, rgb_dev, &f);
   if (st != TSDF_OK) return st;
   if (vol->poisoned) return TSDF_ERR_POISONED;
-  cudaError_t e = tsdf::launch_allocate(f, vol->va, vol->probe_load, as_stream(stream));
+  if (vol->fuse_mode != 0)
+    return from_cuda(
+        tsdf::launch_fused(f, vol->va, vol->probe_load, vol->fuse_mode, as_stream(stream)));
+  cudaError_t e = tsdf::launch_allocate(f, vol->va, vol->probe_load, vol->allocate_mode,
+                                        as_stream(stream));
   if (e == cudaSuccess) e = tsdf::launch_integrate(f, vol->va, vol->integrate_mode,
                                                    as_stream(stream));
   return from_cuda(e);

@@ -138,16 +138,20 @@ __device__ __forceinline__ bool sample_voxel(const FrameArgs& f, const Ray& r, i
 
 // Occlusion test at the voxel centre, shared by both stages (Section 2.2):
 // centre in front of the camera, nearest pixel inside the image with a valid
-// depth d', centre no more than tau behind d'. On success zc = centre's
-// camera-frame depth.
-__device__ __forceinline__ bool voxel_test(const FrameArgs& f, int gx, int gy, int gz,
-                                           float& zc) {
+// depth d', centre no more than tau behind d'. Split in two so that a caller
+// can issue the depth gathers of several samples before testing any of them:
+// voxel_project computes the centre's camera depth zc and the row-major index
+// of its nearest pixel (-1 when behind the camera or outside the image);
+// voxel_accept takes the gathered d'.
+__device__ __forceinline__ int voxel_project(const FrameArgs& f, int gx, int gy, int gz,
+                                             float& zc) {
   const float ex = __fsub_rn(__fmul_rn(__fadd_rn(static_cast<float>(gx), 0.5f), f.v), f.t[0]);
   const float ey = __fsub_rn(__fmul_rn(__fadd_rn(static_cast<float>(gy), 0.5f), f.v), f.t[1]);
   const float ez = __fsub_rn(__fmul_rn(__fadd_rn(static_cast<float>(gz), 0.5f), f.v), f.t[2]);
   // R^T e: column j of R is R[j], R[3+j], R[6+j]
   const float ccz = __fmaf_rn(f.R[8], ez, __fmaf_rn(f.R[5], ey, __fmul_rn(f.R[2], ex)));
-  if (!(ccz > 0.0f)) return false;
+  zc = ccz;
+  if (!(ccz > 0.0f)) return -1;
   const float ccx = __fmaf_rn(f.R[6], ez, __fmaf_rn(f.R[3], ey, __fmul_rn(f.R[0], ex)));
   const float ccy = __fmaf_rn(f.R[7], ez, __fmaf_rn(f.R[4], ey, __fmul_rn(f.R[1], ex)));
   const float iz = __frcp_rn(ccz);
@@ -155,12 +159,82 @@ __device__ __forceinline__ bool voxel_test(const FrameArgs& f, int gx, int gy, i
   const float qv = floorf(__fadd_rn(__fmaf_rn(f.fy, __fmul_rn(ccy, iz), f.cy), 0.5f));
   if (!(qu >= 0.0f && qu < static_cast<float>(f.W) && qv >= 0.0f &&
         qv < static_cast<float>(f.H)))
-    return false;
-  const float d2 = __ldg(f.depth + static_cast<int>(qv) * f.W + static_cast<int>(qu));
-  if (!(isfinite(d2) && d2 > 0.0f)) return false;
-  if (!(__fsub_rn(d2, ccz) >= f.neg_tau)) return false;
-  zc = ccz;
-  return true;
+    return -1;
+  return static_cast<int>(qv) * f.W + static_cast<int>(qu);
+}
+
+__device__ __forceinline__ bool voxel_accept(const FrameArgs& f, float d2, float zc) {
+  return isfinite(d2) && d2 > 0.0f && __fsub_rn(d2, zc) >= f.neg_tau;
+}
+
+__device__ __forceinline__ bool voxel_test(const FrameArgs& f, int gx, int gy, int gz,
+                                           float& zc) {
+  const int q = voxel_project(f, gx, gy, gz, zc);
+  if (q < 0) return false;
+  return voxel_accept(f, __ldg(f.depth + q), zc);
+}
+
+// The band walk of one point with the half band M known at compile time: all
+// 2M+1 samples are unrolled, their depth gathers are issued together, and the
+// result is a mask of accepted samples (after the once-per-point dedupe of
+// voxels) with each sample's voxel and centre depth. Two samples are v apart
+// on a unit ray while a voxel's diagonal is v*sqrt(3) < 2v, so only the
+// previous two in-range samples can repeat a voxel.
+template <int M>
+struct Walk {
+  static constexpr int K = 2 * M + 1;
+  int gx[K], gy[K], gz[K];
+  float zc[K];
+};
+
+template <int M>
+__device__ __forceinline__ unsigned walk_point(const FrameArgs& f, const Ray& r, Walk<M>& w) {
+  constexpr int K = 2 * M + 1;
+  int q[K];
+  unsigned in_range = 0;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const float tk = __fmul_rn(static_cast<float>(k - M), f.v);
+    const float sx = __fmaf_rn(tk, r.dx, r.px);
+    const float sy = __fmaf_rn(tk, r.dy, r.py);
+    const float sz = __fmaf_rn(tk, r.dz, r.pz);
+    const float wx = __fmaf_rn(f.R[2], sz, __fmaf_rn(f.R[1], sy, __fmaf_rn(f.R[0], sx, f.t[0])));
+    const float wy = __fmaf_rn(f.R[5], sz, __fmaf_rn(f.R[4], sy, __fmaf_rn(f.R[3], sx, f.t[1])));
+    const float wz = __fmaf_rn(f.R[8], sz, __fmaf_rn(f.R[7], sy, __fmaf_rn(f.R[6], sx, f.t[2])));
+    const float qx = floorf(__fmul_rn(wx, f.inv_v));
+    const float qy = floorf(__fmul_rn(wy, f.inv_v));
+    const float qz = floorf(__fmul_rn(wz, f.inv_v));
+    const bool ok = (qx >= -kVoxelLimit) && (qx < kVoxelLimit) && (qy >= -kVoxelLimit) &&
+                    (qy < kVoxelLimit) && (qz >= -kVoxelLimit) && (qz < kVoxelLimit);
+    w.gx[k] = ok ? static_cast<int>(qx) : 0;
+    w.gy[k] = ok ? static_cast<int>(qy) : 0;
+    w.gz[k] = ok ? static_cast<int>(qz) : 0;
+    bool fresh = ok;
+    if (k >= 1)
+      fresh = fresh && !(((in_range >> (k - 1)) & 1u) && w.gx[k] == w.gx[k - 1] &&
+                         w.gy[k] == w.gy[k - 1] && w.gz[k] == w.gz[k - 1]);
+    if (k >= 2)
+      fresh = fresh && !(((in_range >> (k - 2)) & 1u) && w.gx[k] == w.gx[k - 2] &&
+                         w.gy[k] == w.gy[k - 2] && w.gz[k] == w.gz[k - 2]);
+    in_range |= ok ? (1u << k) : 0u;
+    q[k] = fresh ? voxel_project(f, w.gx[k], w.gy[k], w.gz[k], w.zc[k]) : -1;
+  }
+  float d2[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) d2[k] = q[k] >= 0 ? __ldg(f.depth + q[k]) : 0.0f;
+  unsigned acc = 0;
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+    acc |= (q[k] >= 0 && voxel_accept(f, d2[k], w.zc[k])) ? (1u << k) : 0u;
+  return acc;
+}
+
+// Fire-and-forget float addition into the pool (PTX `red`): the thread never
+// waits for a returned value. Written explicitly because a plain atomicAdd
+// whose result is unused may still be issued as a returning atomic when the
+// kernel holds other atomics.
+__device__ __forceinline__ void red_add(float* p, float v) {
+  asm volatile("red.relaxed.gpu.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
 }
 
 // Stored value: truncated, normalised signed distance at the voxel centre.
@@ -237,7 +311,10 @@ static __device__ __noinline__ int wait_published(const VolumeArgs& vol, const E
 // set slot never changes, so if it holds our key this is a hit; moving on
 // would duplicate the key). The scan is bounded only by the table size; a full
 // scan reports TABLE_FULL. Returns the pool index or -1 on error.
-template <int P>
+// WAIT = false is the stage-A form used by fallbacks of the tile kernel: a
+// thread that finds its key returns without waiting (returns 0), and the
+// winner publishes without a fence (see warp_insert_nowait).
+template <int P, bool WAIT = true>
 __device__ int insert_block(const VolumeArgs& vol, unsigned long long key, int bx, int by,
                             int bz) {
   unsigned int s = hash_block(bx, by, bz) & vol.mask;
@@ -259,14 +336,17 @@ __device__ int insert_block(const VolumeArgs& vol, unsigned long long key, int b
         c[0] = bx;
         c[1] = by;
         c[2] = bz;
-        __threadfence();  // coordinates visible before the index
+        if (WAIT) __threadfence();  // coordinates visible before the index
         atomicExch(&e->idx, static_cast<int>(i));
         return static_cast<int>(i);
       }
       k = prev;
       idx = kUnpublished;
     }
-    if (k == key) return idx >= 0 ? idx : wait_published(vol, e);
+    if (k == key) {
+      if (!WAIT) return 0;
+      return idx >= 0 ? idx : wait_published(vol, e);
+    }
     // a poisoned volume stops long scans early
     if ((probe & 255u) == 255u &&
         (load_err_volatile(vol.hdr) & (TSDF_ERRBIT_POOL_FULL | TSDF_ERRBIT_TABLE_FULL)))
@@ -276,19 +356,183 @@ __device__ int insert_block(const VolumeArgs& vol, unsigned long long key, int b
   return -1;
 }
 
+// Stage A insert without waiting, warp-cooperative: every lane of the warp
+// calls it, each with at most one key (`has`). The probe and compare-exchange
+// follow Listing 1 (Section 2.3) with the lost-CAS reading (re-examine the
+// slot with the key that won it). Two differences, both safe because stage A
+// is a pass of its own:
+//  * a lane that finds its key already present returns at once: nothing in
+//    this pass consumes the index, and the kernel boundary publishes every
+//    index before stage B reads any;
+//  * the lanes that win a slot in the same probe step take their pool indices
+//    with ONE atomicAdd on the block counter (warp aggregation), and store the
+//    index without a fence (no reader in this pass needs coordinates before
+//    the index).
+template <int P>
+__device__ void warp_insert_nowait(const VolumeArgs& vol, unsigned long long key, bool has) {
+  const unsigned lane = threadIdx.x & 31u;
+  int bx = 0, by = 0, bz = 0;
+  if (has) unpack_key(key, bx, by, bz);
+  unsigned int s = has ? (hash_block(bx, by, bz) & vol.mask) : 0u;
+  bool todo = has;
+  unsigned int probe = 0;
+  while (__any_sync(0xffffffffu, todo)) {
+    bool won = false;
+    Entry* e = vol.table + s;
+    if (todo) {
+      unsigned long long k;
+      int idx;
+      load_entry<P>(e, k, idx);
+      if (k == kEmptyKey) {
+        const unsigned long long prev = atomicCAS(&e->key, kEmptyKey, key);
+        if (prev == kEmptyKey) {
+          won = true;
+          todo = false;
+        } else {
+          k = prev;
+        }
+      }
+      if (todo) {
+        if (k == key) {
+          todo = false;
+        } else {
+          s = (s + 1) & vol.mask;
+          if (++probe >= vol.slots) {
+            atomicOr(&vol.hdr->err, TSDF_ERRBIT_TABLE_FULL);
+            todo = false;
+          } else if ((probe & 255u) == 0u &&
+                     (load_err_volatile(vol.hdr) &
+                      (TSDF_ERRBIT_POOL_FULL | TSDF_ERRBIT_TABLE_FULL))) {
+            todo = false;
+          }
+        }
+      }
+    }
+    const unsigned wins = __ballot_sync(0xffffffffu, won);
+    if (wins) {
+      const int leader = __ffs(wins) - 1;
+      unsigned base = 0;
+      if (static_cast<int>(lane) == leader) base = atomicAdd(&vol.hdr->count, __popc(wins));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (won) {
+        const unsigned i = base + __popc(wins & ((1u << lane) - 1u));
+        if (i >= vol.pool) {
+          atomicOr(&vol.hdr->err, TSDF_ERRBIT_POOL_FULL);
+          atomicExch(&e->idx, kFailedIdx);
+        } else {
+          int32_t* c = vol.coords + 3 * static_cast<size_t>(i);
+          c[0] = bx;
+          c[1] = by;
+          c[2] = bz;
+          *reinterpret_cast<volatile int*>(&e->idx) = static_cast<int>(i);
+        }
+      }
+    }
+  }
+}
+
+// Stage A/fused insert that also yields the index, warp-cooperative: like
+// warp_insert_nowait, but a lane that finds its key waits (bounded) for the
+// winner to publish the index. Returns the pool index, or -1 on error (the
+// error bit is set).
+template <int P>
+__device__ int warp_insert_get(const VolumeArgs& vol, unsigned long long key, bool has) {
+  const unsigned lane = threadIdx.x & 31u;
+  int bx = 0, by = 0, bz = 0;
+  if (has) unpack_key(key, bx, by, bz);
+  unsigned int s = has ? (hash_block(bx, by, bz) & vol.mask) : 0u;
+  bool todo = has;
+  unsigned int probe = 0;
+  int result = -1;
+  const Entry* hit = nullptr;
+  while (__any_sync(0xffffffffu, todo)) {
+    bool won = false;
+    Entry* e = vol.table + s;
+    if (todo) {
+      unsigned long long k;
+      int idx;
+      load_entry<P>(e, k, idx);
+      if (k == kEmptyKey) {
+        const unsigned long long prev = atomicCAS(&e->key, kEmptyKey, key);
+        if (prev == kEmptyKey) {
+          won = true;
+          todo = false;
+        } else {
+          k = prev;
+          idx = kUnpublished;
+        }
+      }
+      if (todo) {
+        if (k == key) {
+          todo = false;
+          if (idx >= 0)
+            result = idx;
+          else if (idx == kUnpublished)
+            hit = e;  // wait below, outside the cooperative loop
+        } else {
+          s = (s + 1) & vol.mask;
+          if (++probe >= vol.slots) {
+            atomicOr(&vol.hdr->err, TSDF_ERRBIT_TABLE_FULL);
+            todo = false;
+          } else if ((probe & 255u) == 0u &&
+                     (load_err_volatile(vol.hdr) &
+                      (TSDF_ERRBIT_POOL_FULL | TSDF_ERRBIT_TABLE_FULL))) {
+            todo = false;
+          }
+        }
+      }
+    }
+    const unsigned wins = __ballot_sync(0xffffffffu, won);
+    if (wins) {
+      const int leader = __ffs(wins) - 1;
+      unsigned base = 0;
+      if (static_cast<int>(lane) == leader) base = atomicAdd(&vol.hdr->count, __popc(wins));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (won) {
+        const unsigned i = base + __popc(wins & ((1u << lane) - 1u));
+        if (i >= vol.pool) {
+          atomicOr(&vol.hdr->err, TSDF_ERRBIT_POOL_FULL);
+          atomicExch(&e->idx, kFailedIdx);
+        } else {
+          int32_t* c = vol.coords + 3 * static_cast<size_t>(i);
+          c[0] = bx;
+          c[1] = by;
+          c[2] = bz;
+          // Readers in this pass use the index only to address the pool, never
+          // the coordinates, so no fence is needed before publishing it.
+          atomicExch(&e->idx, static_cast<int>(i));
+          result = static_cast<int>(i);
+        }
+      }
+    }
+  }
+  if (hit) result = wait_published(vol, hit);
+  return result;
+}
+
+constexpr int kAbsent = -3;  // lookup: key not in the table
+
 // Read-only lookup for stage B (after stage A's kernel has completed every
 // publication): the table is read through the non-coherent read-only path.
+// Returns the pool index, kFailedIdx (slot won but pool exhausted),
+// kUnpublished (claimed but never published: an error) or kAbsent.
 __device__ __forceinline__ int lookup_block(const VolumeArgs& vol, unsigned long long key, int bx,
                                             int by, int bz) {
   unsigned int s = hash_block(bx, by, bz) & vol.mask;
   for (unsigned int probe = 0; probe < vol.slots; ++probe, s = (s + 1) & vol.mask) {
     const ulonglong2 ent = __ldg(reinterpret_cast<const ulonglong2*>(vol.table + s));
-    if (ent.x == key) {
-      const int idx = static_cast<int>(static_cast<unsigned int>(ent.y & 0xFFFFFFFFull));
-      return idx >= 0 ? idx : -1;
-    }
-    if (ent.x == kEmptyKey) return -1;
+    if (ent.x == key) return static_cast<int>(static_cast<unsigned int>(ent.y & 0xFFFFFFFFull));
+    if (ent.x == kEmptyKey) return kAbsent;
   }
+  return kAbsent;
+}
+
+// Stage B's view of a lookup: the pool index, or -1 to skip the contribution.
+// A block that stage A claimed but never published cannot receive its
+// contributions; that is reported (as PUBLISH_TIMEOUT), never silent.
+__device__ __forceinline__ int resolve_for_update(const VolumeArgs& vol, int idx) {
+  if (idx >= 0) return idx;
+  if (idx == kUnpublished) atomicOr(&vol.hdr->err, TSDF_ERRBIT_PUBLISH_TIMEOUT);
   return -1;
 }
 

@@ -1,15 +1,25 @@
-// Kernels of hash-blocked TSDF fusion (paper Section 2.2, "Two passes"):
-//   allocate_kernel   stage A: band walk -> block keys -> per-warp
-//                     __match_any_sync dedupe -> per-CTA shared-memory key set
-//                     -> one insert (Listing 1) per distinct key per CTA;
-//   integrate_*       stage B: band walk -> lookup -> weighted sums into the
-//                     five pool arrays (scatter variant = the paper's update
-//                     stage; aggregated variant = per-CTA shared-memory
-//                     pre-aggregation per voxel, then vector reductions);
-//   export_kernel     read-out: per-voxel means (Section 2.2, sums -> means);
-//   clear_used_kernel reset of the used prefix of the pool.
-// A CTA covers a 16x16 pixel tile; each warp an 8x4 sub-tile, so the lanes of a
-// warp see neighbouring rays and mostly the same blocks.
+// Kernels of hash-blocked TSDF fusion (paper Section 2.2, "Two passes").
+//
+// warp_kernel<Op> (default for every operation): each warp covers an 8x4 pixel
+// patch and works alone, with no shared memory and no barriers --
+//   1. every lane walks its point's band (unrolled when the half band M is
+//      compiled) and keeps each accepted voxel packed with its tsdf value;
+//   2. the warp dedupes the first three distinct blocks of every point with
+//      __match_any_sync, compacts the leaders' keys into lanes and resolves
+//      them in one warp-cooperative pass: stage A inserts (Listing 1 probe and
+//      compare-exchange, counter increments aggregated per warp, no waiting),
+//      stage B looks up, the fused kernel inserts and obtains the indices;
+//   3. stage B and the fused kernel add five sums per accepted voxel with
+//      fire-and-forget reductions.
+// tile_allocate_kernel: stage A with a shared-memory key set per 16x16 tile.
+// The paper's own shapes are kept as strategy 0 of each stage:
+//   allocate_kernel: Listing 1 per sample after a warp dedupe, waiting for
+//     publication on a hit;
+//   integrate_scatter_kernel: per-thread lookups and five atomic additions per
+//     accepted voxel.
+// Read-out and reset: export_kernel (means from sums), clear_used_kernel.
+
+#include <algorithm>
 #include <climits>
 #include <cstdint>
 
@@ -20,7 +30,9 @@ namespace tsdf {
 
 constexpr int kThreads = 256;
 constexpr int kTile = 16;
-constexpr int kSetSlots = 2048;  // per-CTA block-key set (16 KB)
+constexpr int kSetSlots = 2048;    // allocate_kernel: per-CTA key set (16 KB)
+constexpr int kTileSet = 1024;     // tile kernel: key set slots (8 KB)
+constexpr int kTileList = 768;     // tile kernel: compact key list (6 KB)
 
 __device__ __forceinline__ void tile_pixel(int tile, int tiles_x, int& u, int& v) {
   const int tx = tile % tiles_x;
@@ -42,9 +54,7 @@ __device__ __forceinline__ bool set_insert(unsigned long long* set, unsigned lon
   return false;
 }
 
-// Walk state of one point: the last two in-range voxels (two band samples are
-// v apart on a unit ray, a voxel's diagonal is v*sqrt(3) < 2v, so only the
-// previous two samples can repeat a voxel).
+// Walk state of one point for the generic loop: the last two in-range voxels.
 struct WalkDedupe {
   int ax = INT_MIN, ay = 0, az = 0, bx = INT_MIN, by = 0, bz = 0;
   __device__ __forceinline__ bool seen_then_push(int x, int y, int z) {
@@ -55,8 +65,12 @@ struct WalkDedupe {
   }
 };
 
+__device__ __forceinline__ unsigned long long block_key_of(int gx, int gy, int gz) {
+  return pack_key(gx >> 3, gy >> 3, gz >> 3);
+}
+
 // ----------------------------------------------------------------------------
-// stage A
+// stage A, the paper's protocol (Listing 1 per sample, waits for publication)
 // ----------------------------------------------------------------------------
 template <int P>
 __global__ void __launch_bounds__(kThreads)
@@ -106,7 +120,6 @@ __global__ void __launch_bounds__(kThreads)
     }
   }
   __syncthreads();
-  // one global insert per distinct block of the tile
   for (int i = threadIdx.x; i < kSetSlots; i += kThreads) {
     const unsigned long long key = s_set[i];
     if (key != kEmptyKey) {
@@ -117,9 +130,236 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
+// One-entry cache of a resolved block.
+struct BlockCacheT {
+  unsigned long long key = kEmptyKey;
+  int idx = -1;
+};
+
+// ----------------------------------------------------------------------------
+// tile machinery shared by the tile kernels (stage A, stage B, fused)
+// ----------------------------------------------------------------------------
+// The distinct block keys of a 16x16 pixel tile live in a shared-memory set;
+// the first thread to add a key appends it to a compact list. Each warp then
+// resolves (inserts or looks up) the keys it appended in one warp-cooperative
+// pass, so no CTA-wide barrier waits on a global round trip.
+struct TileShared {
+  unsigned long long set[kTileSet];
+  unsigned long long list[kTileList];
+  short pos[kTileSet];                 // list position of set[s], -1 if it did not fit
+  int n;
+  unsigned int err;
+};
+
+__device__ __forceinline__ unsigned int tile_hash(unsigned long long key) {
+  return static_cast<unsigned int>((key * 0x9E3779B97F4A7C15ull) >> 40);
+}
+
+// Add a key. Returns its list position when this call appended it, -1 when it
+// could not be listed (set or list full), -2 when it was already present.
+__device__ __forceinline__ int tile_add(TileShared& T, unsigned long long key) {
+  const unsigned int h = tile_hash(key);
+  for (int i = 0; i < kTileSet; ++i) {
+    const unsigned int s = (h + i) & (kTileSet - 1);
+    const unsigned long long prev = atomicCAS(&T.set[s], kEmptyKey, key);
+    if (prev == kEmptyKey) {
+      int p = atomicAdd(&T.n, 1);
+      if (p < kTileList)
+        T.list[p] = key;
+      else
+        p = -1;
+      T.pos[s] = static_cast<short>(p);
+      return p;
+    }
+    if (prev == key) return -2;
+  }
+  return -1;
+}
+
+// List position of a key after the set is complete (after a barrier); -1 if
+// the key is not listed.
+__device__ __forceinline__ int tile_find(const TileShared& T, unsigned long long key) {
+  const unsigned int h = tile_hash(key);
+  for (int i = 0; i < kTileSet; ++i) {
+    const unsigned int s = (h + i) & (kTileSet - 1);
+    const unsigned long long k = T.set[s];
+    if (k == key) return T.pos[s];
+    if (k == kEmptyKey) return -1;
+  }
+  return -1;
+}
+
+// Distinct accepted blocks of one point, in walk order: up to three in
+// registers, any further ones straight into the tile set.
+struct PointKeys {
+  unsigned long long k0 = kEmptyKey, k1 = kEmptyKey, k2 = kEmptyKey, last = kEmptyKey;
+  int n = 0;
+};
+
+enum TileOp { kOpAllocate = 0, kOpIntegrate = 1, kOpFused = 2 };
+
+// Resolve one key on its own (paths that could not use the tile list).
+template <int Op, int P>
+__device__ __forceinline__ int resolve_single(const VolumeArgs& vol, unsigned long long key) {
+  int bx, by, bz;
+  unpack_key(key, bx, by, bz);
+  if (Op == kOpAllocate) return insert_block<P, false>(vol, key, bx, by, bz);
+  if (Op == kOpFused) return insert_block<P, true>(vol, key, bx, by, bz);
+  return resolve_for_update(vol, lookup_block(vol, key, bx, by, bz));
+}
+
+template <int Op, int P>
+__device__ __forceinline__ void point_key(PointKeys& pk, unsigned long long key, TileShared& T,
+                                          const VolumeArgs& vol) {
+  if (key == pk.last) return;
+  pk.last = key;
+  if (pk.n == 0) {
+    pk.k0 = key;
+  } else if (pk.n == 1) {
+    pk.k1 = key;
+  } else if (pk.n == 2) {
+    pk.k2 = key;
+  } else {
+    // a fourth or later block of one point: rare; resolved by this thread
+    if (tile_add(T, key) == -1) resolve_single<Op, P>(vol, key);
+  }
+  pk.n++;
+}
+
+__device__ __forceinline__ void tile_init(TileShared& T, const VolumeArgs& vol) {
+  if (threadIdx.x == 0) {
+    T.err = load_err_volatile(vol.hdr);
+    T.n = 0;
+  }
+  for (int i = threadIdx.x; i < kTileSet; i += kThreads) T.set[i] = kEmptyKey;
+}
+
+__device__ __forceinline__ bool tile_ray(const FrameArgs& f, int tile, int tiles_x, Ray& r, int& u,
+                                         int& v) {
+  tile_pixel(tile, tiles_x, u, v);
+  if (u >= f.W || v >= f.H) return false;
+  return make_ray(f, u, v, __ldg(f.depth + v * f.W + u), r);
+}
+
+// Phases 1 and 2 of every tile kernel: the point's walk and its distinct
+// accepted blocks; a per-warp __match_any_sync dedupe of each point's first
+// three blocks before the tile set; then each warp resolves the keys it
+// appended to the tile list, warp-cooperatively (stage A: insert without
+// waiting; stage B: look up; fused: insert and obtain the index). Every lane
+// of every warp calls it.
+template <int Op, int P, int M>
+__device__ __forceinline__ void tile_collect(TileShared& T, const FrameArgs& f,
+                                             const VolumeArgs& vol, const Ray& r, bool valid,
+                                             Walk<M>& w, unsigned& acc, PointKeys& pk) {
+  acc = 0;
+  if (valid) {
+    if constexpr (M > 0) {
+      acc = walk_point<M>(f, r, w);
+#pragma unroll
+      for (int k = 0; k < 2 * M + 1; ++k)
+        if ((acc >> k) & 1u) point_key<Op, P>(pk, block_key_of(w.gx[k], w.gy[k], w.gz[k]), T, vol);
+    } else {
+      // Generic half band. For allocation alone, a sample whose block already
+      // holds an accepted voxel of this point cannot add a block, so its test
+      // is skipped; duplicates of a voxel cannot add one either.
+      WalkDedupe walk;
+      for (int k = 0; k <= 2 * f.M; ++k) {
+        int gx, gy, gz;
+        float zc;
+        if (!sample_voxel(f, r, k, gx, gy, gz)) continue;
+        const unsigned long long key = block_key_of(gx, gy, gz);
+        if (Op == kOpAllocate) {
+          if (key == pk.last) continue;
+        } else if (walk.seen_then_push(gx, gy, gz)) {
+          continue;
+        }
+        if (voxel_test(f, gx, gy, gz, zc)) point_key<Op, P>(pk, key, T, vol);
+      }
+    }
+  }
+  const unsigned lane = threadIdx.x & 31u;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const unsigned long long key = j == 0 ? pk.k0 : (j == 1 ? pk.k1 : pk.k2);
+    const bool has = pk.n > j;
+    const unsigned m = __ballot_sync(0xffffffffu, has);
+    if (has) {
+      const unsigned peers = __match_any_sync(m, key);
+      if (lane == static_cast<unsigned>(__ffs(peers) - 1)) {
+        // a key that cannot be listed is inserted by its adder at once
+        if (tile_add(T, key) == -1) resolve_single<Op, P>(vol, key);
+      }
+    }
+  }
+}
+
+// Five sums of one accepted voxel, added straight to the pool.
+__device__ __forceinline__ void add_voxel_direct(const VolumeArgs& vol, int idx, int l, float t,
+                                                 bool colour, float cr, float cg, float cb) {
+  if (idx < 0) return;
+  const size_t o = static_cast<size_t>(idx) * kBlockVoxels + l;
+  red_add(vol.ch[0] + o, t);
+  red_add(vol.ch[1] + o, 1.0f);
+  if (colour) {
+    red_add(vol.ch[2] + o, cr);
+    red_add(vol.ch[3] + o, cg);
+    red_add(vol.ch[4] + o, cb);
+  }
+}
+
+// Stage A, tile strategy: one CTA per 16x16 pixel tile; the tile's distinct
+// keys are collected in the shared-memory set, then, after one barrier, the
+// list is inserted by consecutive lanes, warp-cooperatively, without waiting.
+template <int P, int M>
+__global__ void __launch_bounds__(kThreads)
+    tile_allocate_kernel(const __grid_constant__ FrameArgs f,
+                         const __grid_constant__ VolumeArgs vol, int tiles_x) {
+  __shared__ TileShared T;
+  tile_init(T, vol);
+  __syncthreads();
+  if (T.err) return;  // poisoned volume: do nothing (uniform across the CTA)
+  Ray r;
+  int u, v;
+  const bool valid = tile_ray(f, blockIdx.x, tiles_x, r, u, v);
+  Walk<M> w;
+  unsigned acc;
+  PointKeys pk;
+  tile_collect<kOpAllocate, P, M>(T, f, vol, r, valid, w, acc, pk);
+  __syncthreads();
+  const int n = T.n < kTileList ? T.n : kTileList;
+  const unsigned lane = threadIdx.x & 31u;
+  for (int base = (threadIdx.x & ~31); base < n; base += kThreads) {
+    const int i = base + static_cast<int>(lane);
+    const bool has = i < n;
+    warp_insert_nowait<P>(vol, has ? T.list[i] : kEmptyKey, has);
+  }
+}
+
 // ----------------------------------------------------------------------------
 // stage B, scatter: five atomic additions per accepted voxel (Section 2.2)
 // ----------------------------------------------------------------------------
+__device__ __forceinline__ void scatter_add(const FrameArgs& f, const VolumeArgs& vol,
+                                            BlockCacheT& bc, const Ray& r, int gx, int gy, int gz,
+                                            float zc, bool colour, float cr, float cg,
+                                            float cb) {
+  const int bx = gx >> 3, by = gy >> 3, bz = gz >> 3;
+  const unsigned long long key = pack_key(bx, by, bz);
+  if (key != bc.key) {
+    bc.key = key;
+    bc.idx = resolve_for_update(vol, lookup_block(vol, key, bx, by, bz));
+  }
+  if (bc.idx < 0) return;
+  const size_t o = static_cast<size_t>(bc.idx) * kBlockVoxels + local_index(gx, gy, gz);
+  red_add(vol.ch[0] + o, tsdf_value(f, r.d, zc));
+  red_add(vol.ch[1] + o, 1.0f);
+  if (colour) {
+    red_add(vol.ch[2] + o, cr);
+    red_add(vol.ch[3] + o, cg);
+    red_add(vol.ch[4] + o, cb);
+  }
+}
+
+template <int M>
 __global__ void __launch_bounds__(kThreads)
     integrate_scatter_kernel(const __grid_constant__ FrameArgs f,
                              const __grid_constant__ VolumeArgs vol, int tiles_x) {
@@ -141,29 +381,23 @@ __global__ void __launch_bounds__(kThreads)
     cg = static_cast<float>(c[1]);
     cb = static_cast<float>(c[2]);
   }
-  unsigned long long ckey = kEmptyKey;
-  int cidx = -1;
-  WalkDedupe walk;
-  for (int k = 0; k <= 2 * f.M; ++k) {
-    int gx, gy, gz;
-    float zc;
-    if (!sample_voxel(f, r, k, gx, gy, gz) || walk.seen_then_push(gx, gy, gz) ||
-        !voxel_test(f, gx, gy, gz, zc))
-      continue;
-    const int bx = gx >> 3, by = gy >> 3, bz = gz >> 3;
-    const unsigned long long key = pack_key(bx, by, bz);
-    if (key != ckey) {
-      ckey = key;
-      cidx = lookup_block(vol, key, bx, by, bz);
-    }
-    if (cidx < 0) continue;
-    const size_t o = static_cast<size_t>(cidx) * kBlockVoxels + local_index(gx, gy, gz);
-    atomicAdd(vol.ch[0] + o, tsdf_value(f, r.d, zc));
-    atomicAdd(vol.ch[1] + o, 1.0f);
-    if (colour) {
-      atomicAdd(vol.ch[2] + o, cr);
-      atomicAdd(vol.ch[3] + o, cg);
-      atomicAdd(vol.ch[4] + o, cb);
+  BlockCacheT bc;
+  if constexpr (M > 0) {
+    Walk<M> w;
+    const unsigned acc = walk_point<M>(f, r, w);
+#pragma unroll
+    for (int k = 0; k < 2 * M + 1; ++k)
+      if ((acc >> k) & 1u)
+        scatter_add(f, vol, bc, r, w.gx[k], w.gy[k], w.gz[k], w.zc[k], colour, cr, cg, cb);
+  } else {
+    WalkDedupe walk;
+    for (int k = 0; k <= 2 * f.M; ++k) {
+      int gx, gy, gz;
+      float zc;
+      if (!sample_voxel(f, r, k, gx, gy, gz) || walk.seen_then_push(gx, gy, gz) ||
+          !voxel_test(f, gx, gy, gz, zc))
+        continue;
+      scatter_add(f, vol, bc, r, gx, gy, gz, zc, colour, cr, cg, cb);
     }
   }
 }
@@ -204,38 +438,347 @@ __global__ void clear_used_kernel(const __grid_constant__ VolumeArgs vol) {
   }
 }
 
-// ----------------------------------------------------------------------------
-// launchers
-// ----------------------------------------------------------------------------
 static inline int tiles_of(int n) { return (n + kTile - 1) / kTile; }
 
-cudaError_t launch_allocate(const FrameArgs& f, const VolumeArgs& vol, int probe_load,
+// ----------------------------------------------------------------------------
+// warp kernels: barrier-free stage A / stage B / fused
+// ----------------------------------------------------------------------------
+// Each warp covers an 8x4 pixel patch and works alone: its lanes walk their
+// bands, the warp dedupes the first three distinct blocks of every point with
+// __match_any_sync, compacts the leaders' keys of all three rounds into lanes
+// 0..n-1, resolves them in one warp-cooperative pass (insert without waiting,
+// look up, or insert and obtain the index), and shuffles the indices back to
+// every lane that needs them. Stage B and the fused kernel then add five sums
+// per accepted voxel straight to the pool. No shared memory, no barriers:
+// occupancy is bounded by registers alone, and every warp overlaps its global
+// round trips with other warps' walks.
+template <int Op, int P>
+__device__ __forceinline__ int warp_resolve(const VolumeArgs& vol, unsigned long long key,
+                                            bool has) {
+  if (Op == kOpAllocate) {
+    warp_insert_nowait<P>(vol, key, has);
+    return -1;
+  }
+  if (Op == kOpFused) return warp_insert_get<P>(vol, key, has);
+  if (!has) return -1;
+  int bx, by, bz;
+  unpack_key(key, bx, by, bz);
+  return resolve_for_update(vol, lookup_block(vol, key, bx, by, bz));
+}
+
+// A point's accepted voxel after phase 1, packed: local index (9 bits), which
+// of the point's first three blocks it lies in (2 bits), valid flag.
+constexpr unsigned kPackValid = 1u << 11;
+
+// A fourth or later block of one point (rare): handled by its own thread at
+// once -- inserted (stage A), or resolved and its voxel added (stage B, fused).
+template <int Op, int P>
+__device__ __noinline__ void extra_block_voxel(const FrameArgs& f, const VolumeArgs& vol,
+                                               unsigned long long key, int l, float t,
+                                               int pu, int pv) {
+  const int idx = resolve_single<Op, P>(vol, key);
+  if (Op == kOpAllocate) return;
+  const bool colour = f.rgb != nullptr;
+  float cr = 0.0f, cg = 0.0f, cb = 0.0f;
+  if (colour) {
+    const uint8_t* c = f.rgb + 3 * (static_cast<size_t>(pv) * f.W + pu);
+    cr = c[0];
+    cg = c[1];
+    cb = c[2];
+  }
+  add_voxel_direct(vol, idx, l, t, colour, cr, cg, cb);
+}
+
+template <int Op, int P, int M>
+__device__ __forceinline__ void warp_body(const FrameArgs& f, const VolumeArgs& vol,
+                                          int tiles_x) {
+  if (load_err_volatile(vol.hdr)) return;  // poisoned volume: do nothing
+  const unsigned lane = threadIdx.x & 31u;
+  int u, v;
+  tile_pixel(blockIdx.x, tiles_x, u, v);
+  Ray r;
+  const bool valid = u < f.W && v < f.H && make_ray(f, u, v, __ldg(f.depth + v * f.W + u), r);
+
+  // phase 1: walk; the point's first three distinct accepted blocks; every
+  // accepted voxel packed as (local index, block slot) with its tsdf value
+  constexpr int K = M > 0 ? 2 * M + 1 : 1;
+  unsigned pack[K];
+  float tv[K];
+  unsigned long long key[3] = {kEmptyKey, kEmptyKey, kEmptyKey};
+  unsigned long long last = kEmptyKey;
+  int nk = 0;
+  auto take = [&](unsigned long long kk, int l, float t) -> unsigned {
+    if (kk != last) {
+      last = kk;
+      if (nk == 0)
+        key[0] = kk;
+      else if (nk == 1)
+        key[1] = kk;
+      else if (nk == 2)
+        key[2] = kk;
+      ++nk;
+    }
+    if (kk == key[0]) return kPackValid | static_cast<unsigned>(l);
+    if (kk == key[1]) return kPackValid | (1u << 9) | static_cast<unsigned>(l);
+    if (kk == key[2]) return kPackValid | (2u << 9) | static_cast<unsigned>(l);
+    extra_block_voxel<Op, P>(f, vol, kk, l, t, u, v);
+    return 0u;
+  };
+  if constexpr (M > 0) {
+    if (valid) {
+      Walk<M> w;
+      const unsigned acc = walk_point<M>(f, r, w);
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        pack[k] = 0u;
+        tv[k] = 0.0f;
+        if ((acc >> k) & 1u) {
+          tv[k] = tsdf_value(f, r.d, w.zc[k]);
+          pack[k] = take(block_key_of(w.gx[k], w.gy[k], w.gz[k]),
+                         local_index(w.gx[k], w.gy[k], w.gz[k]), tv[k]);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        pack[k] = 0u;
+        tv[k] = 0.0f;
+      }
+    }
+  } else if (valid) {
+    // generic half band: keys only here, voxels are re-walked in phase 3
+    WalkDedupe walk;
+    for (int k = 0; k <= 2 * f.M; ++k) {
+      int gx, gy, gz;
+      float zc;
+      if (!sample_voxel(f, r, k, gx, gy, gz)) continue;
+      const unsigned long long kk = block_key_of(gx, gy, gz);
+      if (Op == kOpAllocate) {
+        if (kk == last) continue;
+      } else if (walk.seen_then_push(gx, gy, gz)) {
+        continue;
+      }
+      if (!voxel_test(f, gx, gy, gz, zc)) continue;
+      if (kk == last) continue;
+      last = kk;
+      if (nk == 0)
+        key[0] = kk;
+      else if (nk == 1)
+        key[1] = kk;
+      else if (nk == 2)
+        key[2] = kk;
+      else if (Op == kOpAllocate)
+        resolve_single<kOpAllocate, P>(vol, kk);
+      ++nk;
+    }
+  }
+
+  // phase 2: warp dedupe of each round, compaction of the leaders, one
+  // cooperative resolution, indices back to every lane
+  unsigned leaders[3], leader_of[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const bool has = nk > j;
+    const unsigned m = __ballot_sync(0xffffffffu, has);
+    unsigned peers = 0;
+    if (has) peers = __match_any_sync(m, key[j]);
+    leader_of[j] = has ? static_cast<unsigned>(__ffs(peers) - 1) : 0u;
+    leaders[j] = __ballot_sync(0xffffffffu, has && leader_of[j] == lane);
+  }
+  const int n0 = __popc(leaders[0]), n1 = __popc(leaders[1]), n2 = __popc(leaders[2]);
+  const int n = n0 + n1 + n2;
+  int idx[3] = {-1, -1, -1};
+  int c_of[3];  // compact index of the entry that resolves this lane's key j
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const int base = j == 0 ? 0 : (j == 1 ? n0 : n0 + n1);
+    c_of[j] = base + __popc(leaders[j] & ((1u << leader_of[j]) - 1u));
+  }
+  for (int chunk = 0; chunk < n; chunk += 32) {
+    const int c = chunk + static_cast<int>(lane);
+    const bool has = c < n;
+    int j = 2, rank = c - n0 - n1;
+    if (c < n0) {
+      j = 0;
+      rank = c;
+    } else if (c < n0 + n1) {
+      j = 1;
+      rank = c - n0;
+    }
+    const unsigned src0 = __fns(leaders[0], 0, (j == 0 && has ? rank : 0) + 1);
+    const unsigned src1 = __fns(leaders[1], 0, (j == 1 && has ? rank : 0) + 1);
+    const unsigned src2 = __fns(leaders[2], 0, (j == 2 && has ? rank : 0) + 1);
+    const unsigned long long g0 = __shfl_sync(0xffffffffu, key[0], src0 & 31u);
+    const unsigned long long g1 = __shfl_sync(0xffffffffu, key[1], src1 & 31u);
+    const unsigned long long g2 = __shfl_sync(0xffffffffu, key[2], src2 & 31u);
+    const unsigned long long mine = j == 0 ? g0 : (j == 1 ? g1 : g2);
+    const int res = warp_resolve<Op, P>(vol, has ? mine : kEmptyKey, has);
+    if (Op != kOpAllocate) {
+#pragma unroll
+      for (int jj = 0; jj < 3; ++jj) {
+        const int cj = c_of[jj] - chunk;
+        const int got = __shfl_sync(0xffffffffu, res, cj & 31);
+        if (nk > jj && cj >= 0 && cj < 32) idx[jj] = got;
+      }
+    }
+  }
+  if (Op == kOpAllocate || !valid) return;
+
+  // phase 3: five sums per accepted voxel
+  float cr = 0.0f, cg = 0.0f, cb = 0.0f;
+  const bool colour = f.rgb != nullptr;
+  if (colour) {
+    const uint8_t* c = f.rgb + 3 * (static_cast<size_t>(v) * f.W + u);
+    cr = static_cast<float>(c[0]);
+    cg = static_cast<float>(c[1]);
+    cb = static_cast<float>(c[2]);
+  }
+  if constexpr (M > 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      if (pack[k] & kPackValid) {
+        const unsigned slot = (pack[k] >> 9) & 3u;
+        const int id = slot == 0 ? idx[0] : (slot == 1 ? idx[1] : idx[2]);
+        add_voxel_direct(vol, id, static_cast<int>(pack[k] & 511u), tv[k], colour, cr, cg, cb);
+      }
+    }
+  } else {
+    WalkDedupe walk;
+    BlockCacheT slow;
+    for (int k = 0; k <= 2 * f.M; ++k) {
+      int gx, gy, gz;
+      float zc;
+      if (!sample_voxel(f, r, k, gx, gy, gz) || walk.seen_then_push(gx, gy, gz) ||
+          !voxel_test(f, gx, gy, gz, zc))
+        continue;
+      const unsigned long long kk = block_key_of(gx, gy, gz);
+      int id;
+      if (kk == key[0]) {
+        id = idx[0];
+      } else if (kk == key[1]) {
+        id = idx[1];
+      } else if (kk == key[2]) {
+        id = idx[2];
+      } else {
+        if (kk != slow.key) {
+          slow.key = kk;
+          slow.idx = resolve_single<Op, P>(vol, kk);
+        }
+        id = slow.idx;
+      }
+      add_voxel_direct(vol, id, local_index(gx, gy, gz), tsdf_value(f, r.d, zc), colour, cr, cg,
+                       cb);
+    }
+  }
+}
+
+// MinBlocks: the CTAs per SM the register allocation must allow.
+template <int Op, int P, int M, int MinBlocks>
+__global__ void __launch_bounds__(kThreads, MinBlocks)
+    warp_kernel(const __grid_constant__ FrameArgs f, const __grid_constant__ VolumeArgs vol,
+                int tiles_x) {
+  warp_body<Op, P, M>(f, vol, tiles_x);
+}
+
+template <int Op, int P>
+static cudaError_t launch_warp_m(const FrameArgs& f, const VolumeArgs& vol, cudaStream_t s) {
+  const int tx = tiles_of(f.W);
+  const int tiles = tx * tiles_of(f.H);
+  switch (f.M) {
+    case 2: warp_kernel<Op, P, 2, 1><<<tiles, kThreads, 0, s>>>(f, vol, tx); break;
+    case 4: warp_kernel<Op, P, 4, 1><<<tiles, kThreads, 0, s>>>(f, vol, tx); break;
+    case 8: warp_kernel<Op, P, 8, 1><<<tiles, kThreads, 0, s>>>(f, vol, tx); break;
+    default: warp_kernel<Op, P, 0, 1><<<tiles, kThreads, 0, s>>>(f, vol, tx); break;
+  }
+  return cudaGetLastError();
+}
+
+template <int Op>
+static cudaError_t launch_warp_p(const FrameArgs& f, const VolumeArgs& vol, int probe_load,
+                                 cudaStream_t s) {
+  switch (probe_load) {
+    case kLoadL2: return launch_warp_m<Op, kLoadL2>(f, vol, s);
+    case kLoadRelaxed: return launch_warp_m<Op, kLoadRelaxed>(f, vol, s);
+    default: return launch_warp_m<Op, kLoadCached>(f, vol, s);
+  }
+}
+
+template <int P, int M>
+static cudaError_t launch_tile_kernel(const FrameArgs& f, const VolumeArgs& vol,
+                                      cudaStream_t s) {
+  const int tx = tiles_of(f.W);
+  tile_allocate_kernel<P, M><<<tx * tiles_of(f.H), kThreads, 0, s>>>(f, vol, tx);
+  return cudaGetLastError();
+}
+
+template <int P>
+static cudaError_t launch_tile_m(const FrameArgs& f, const VolumeArgs& vol, cudaStream_t s) {
+  switch (f.M) {
+    case 2: return launch_tile_kernel<P, 2>(f, vol, s);
+    case 4: return launch_tile_kernel<P, 4>(f, vol, s);
+    case 8: return launch_tile_kernel<P, 8>(f, vol, s);
+    default: return launch_tile_kernel<P, 0>(f, vol, s);
+  }
+}
+
+static cudaError_t launch_tile_p(const FrameArgs& f, const VolumeArgs& vol, int probe_load,
+                                 cudaStream_t s) {
+  switch (probe_load) {
+    case kLoadL2: return launch_tile_m<kLoadL2>(f, vol, s);
+    case kLoadRelaxed: return launch_tile_m<kLoadRelaxed>(f, vol, s);
+    default: return launch_tile_m<kLoadCached>(f, vol, s);
+  }
+}
+
+cudaError_t launch_allocate(const FrameArgs& f, const VolumeArgs& vol, int probe_load, int mode,
                             cudaStream_t s) {
   const int tx = tiles_of(f.W);
   const int tiles = tx * tiles_of(f.H);
-  switch (probe_load) {
-    case kLoadL2:
-      allocate_kernel<kLoadL2><<<tiles, kThreads, 0, s>>>(f, vol, tx);
-      break;
-    case kLoadRelaxed:
-      allocate_kernel<kLoadRelaxed><<<tiles, kThreads, 0, s>>>(f, vol, tx);
-      break;
-    default:
-      allocate_kernel<kLoadCached><<<tiles, kThreads, 0, s>>>(f, vol, tx);
-      break;
+  cudaError_t e = cudaSuccess;
+  if (mode == 0) {
+    switch (probe_load) {
+      case kLoadL2: allocate_kernel<kLoadL2><<<tiles, kThreads, 0, s>>>(f, vol, tx); break;
+      case kLoadRelaxed:
+        allocate_kernel<kLoadRelaxed><<<tiles, kThreads, 0, s>>>(f, vol, tx);
+        break;
+      default: allocate_kernel<kLoadCached><<<tiles, kThreads, 0, s>>>(f, vol, tx); break;
+    }
+    e = cudaGetLastError();
+  } else if (mode == 1) {
+    e = launch_tile_p(f, vol, probe_load, s);
+  } else {
+    e = launch_warp_p<kOpAllocate>(f, vol, probe_load, s);
   }
   note_launch();
-  return cudaGetLastError();
+  return e;
 }
 
 cudaError_t launch_integrate(const FrameArgs& f, const VolumeArgs& vol, int mode,
                              cudaStream_t s) {
   const int tx = tiles_of(f.W);
   const int tiles = tx * tiles_of(f.H);
-  (void)mode;
-  integrate_scatter_kernel<<<tiles, kThreads, 0, s>>>(f, vol, tx);
+  cudaError_t e = cudaSuccess;
+  if (mode == 0) {
+    switch (f.M) {
+      case 2: integrate_scatter_kernel<2><<<tiles, kThreads, 0, s>>>(f, vol, tx); break;
+      case 4: integrate_scatter_kernel<4><<<tiles, kThreads, 0, s>>>(f, vol, tx); break;
+      case 8: integrate_scatter_kernel<8><<<tiles, kThreads, 0, s>>>(f, vol, tx); break;
+      default: integrate_scatter_kernel<0><<<tiles, kThreads, 0, s>>>(f, vol, tx); break;
+    }
+    e = cudaGetLastError();
+  } else {
+    e = launch_warp_m<kOpIntegrate, kLoadCached>(f, vol, s);
+  }
   note_launch();
-  return cudaGetLastError();
+  return e;
+}
+
+cudaError_t launch_fused(const FrameArgs& f, const VolumeArgs& vol, int probe_load, int mode,
+                         cudaStream_t s) {
+  (void)mode;
+  const cudaError_t e = launch_warp_p<kOpFused>(f, vol, probe_load, s);
+  note_launch();
+  return e;
 }
 
 cudaError_t launch_export(const VolumeArgs& vol, float* out, unsigned int n, cudaStream_t s) {

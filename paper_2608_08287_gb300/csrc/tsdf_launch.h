@@ -11,10 +11,12 @@ namespace tsdf {
 // Launch accounting: every kernel launch the library enqueues is counted.
 void note_launch();
 
-cudaError_t launch_allocate(const FrameArgs& f, const VolumeArgs& vol, int probe_load,
+cudaError_t launch_allocate(const FrameArgs& f, const VolumeArgs& vol, int probe_load, int mode,
                             cudaStream_t s);
 cudaError_t launch_integrate(const FrameArgs& f, const VolumeArgs& vol, int mode,
                              cudaStream_t s);
+cudaError_t launch_fused(const FrameArgs& f, const VolumeArgs& vol, int probe_load, int mode,
+                         cudaStream_t s);
 cudaError_t launch_export(const VolumeArgs& vol, float* out, unsigned int n, cudaStream_t s);
 cudaError_t launch_clear_used(const VolumeArgs& vol, int sm_count, cudaStream_t s);
 

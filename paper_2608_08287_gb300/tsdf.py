@@ -20,7 +20,8 @@ from .build import LIB
 
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OUT_OF_MEMORY", 3: "POOL_FULL", 4: "TABLE_FULL",
           5: "PUBLISH_TIMEOUT", 6: "BOUNDS", 7: "POISONED", 8: "CUDA"}
-OPTIONS = {"probe_load": 0, "publish_timeout_ns": 1, "integrate_mode": 2, "threads": 3}
+OPTIONS = {"probe_load": 0, "publish_timeout_ns": 1, "integrate_mode": 2, "threads": 3,
+           "allocate_mode": 4, "fuse_mode": 5}
 ERRBITS = {"POOL_FULL": 1, "TABLE_FULL": 2, "PUBLISH_TIMEOUT": 4, "BOUNDS": 8}
 EMPTY_KEY = 0xFFFFFFFFFFFFFFFF
 NOALLOC_MAX_PIXELS = 1 << 20

@@ -97,12 +97,26 @@ def test_room_640x480_full_frame():
     assert n == ov.last_stats["unique_blocks"] > 5000
 
 
+# (voxel, truncation) pairs covering half bands M = 4, 3, 4, 5, 2, 8: the
+# unrolled walks (M = 2, 4, 8) and the generic loop (M = 3, 5)
+BANDS = [(0.05, 0.2), (0.1, 0.3), (0.03, 0.12), (0.02, 0.1), (0.04, 0.08), (0.01, 0.08)]
+
+
+# (fuse, allocate, integrate) modes: the fused kernel, and the two-stage path
+# with each stage A and stage B strategy
+MODES = [dict(fuse_mode=1),
+         dict(fuse_mode=0, allocate_mode=2, integrate_mode=1),
+         dict(fuse_mode=0, allocate_mode=1, integrate_mode=1),
+         dict(fuse_mode=0, allocate_mode=0, integrate_mode=0),
+         dict(fuse_mode=0, allocate_mode=1, integrate_mode=0)]
+
+
 @pytest.mark.parametrize("seed", range(64))
 def test_random_tiny_frames(seed):
     f = synth.random_frame(2000 + seed, width=16 + seed % 5, height=12 + seed % 3)
-    v, tau = [(0.05, 0.2), (0.1, 0.3), (0.03, 0.12), (0.02, 0.1)][seed % 4]
+    v, tau = BANDS[seed % len(BANDS)]
     spec = synth.VolumeSpec(v, tau, 1 << 12, 1 << 12)
-    gv, ov = fuse_both([f], spec)
+    gv, ov = fuse_both([f], spec, **MODES[(seed // len(BANDS)) % len(MODES)])
     assert_same_volume(gv, ov)
 
 
@@ -139,16 +153,34 @@ def test_empty_and_invalid_frames():
 # ----------------------------------------------------------------------------
 # variants must not change the result
 # ----------------------------------------------------------------------------
+@pytest.mark.parametrize("mode", range(len(MODES)))
 @pytest.mark.parametrize("policy", [0, 1, 2])
-def test_probe_load_policies(policy):
+def test_probe_load_policies_and_modes(policy, mode):
     gv, ov = fuse_both([synth.room_frame(3, width=320, height=240)],
-                       synth.VolumeSpec(0.005, 0.02, 1 << 16, 1 << 15), probe_load=policy)
+                       synth.VolumeSpec(0.005, 0.02, 1 << 16, 1 << 15), probe_load=policy,
+                       **MODES[mode])
     assert_same_volume(gv, ov)
 
 
-@pytest.mark.parametrize("mode", [0, 1])
-def test_integrate_modes(mode):
-    gv, ov = fuse_both([synth.room_frame(40)], synth.ROOM_640, integrate_mode=mode)
+@pytest.mark.parametrize("mode", range(len(MODES)))
+@pytest.mark.parametrize("band", BANDS)
+def test_half_bands_on_room(band, mode):
+    v, tau = band
+    gv, ov = fuse_both([synth.room_frame(21, width=200, height=150)],
+                       synth.VolumeSpec(v, tau, 1 << 16, 1 << 14), **MODES[mode])
+    assert_same_volume(gv, ov)
+
+
+@pytest.mark.parametrize("mode", range(len(MODES)))
+def test_room_640x480_every_mode(mode):
+    gv, ov = fuse_both([synth.room_frame(40)], synth.ROOM_640, **MODES[mode])
+    assert_same_volume(gv, ov)
+
+
+@pytest.mark.parametrize("mode", range(len(MODES)))
+def test_multi_frame_every_mode(mode):
+    frames = [synth.room_frame(i * 11, width=320, height=240) for i in range(4)]
+    gv, ov = fuse_both(frames, synth.VolumeSpec(0.005, 0.02, 1 << 18, 1 << 16), **MODES[mode])
     assert_same_volume(gv, ov)
 
 
@@ -214,26 +246,28 @@ def high_load_frames(slots, target=0.93, v=0.01, width=160, height=120, step=3):
     return frames
 
 
-def test_high_load_factor_zero_lost_blocks():
+@pytest.mark.parametrize("mode", range(len(MODES)))
+def test_high_load_factor_zero_lost_blocks(mode):
     """Table and pool sized so the final load factor exceeds 0.9: the unbounded
     probe keeps every block (the bounded probe of Section 7.2 loses blocks from a
     load of 0.071 on)."""
     slots = 1 << 12
     frames = high_load_frames(slots)
     spec = synth.VolumeSpec(0.01, 0.04, slots, slots)
-    gv, ov = fuse_both(frames, spec)
+    gv, ov = fuse_both(frames, spec, **MODES[mode])
     n = assert_same_volume(gv, ov)
     assert n / slots > 0.9, n / slots
 
 
+@pytest.mark.parametrize("mode", range(len(MODES)))
 @pytest.mark.parametrize("pool", [1, 4, 16, "D-1"])
-def test_pool_overflow_reported(pool):
+def test_pool_overflow_reported(pool, mode):
     f = synth.plane_sphere_frame()
     spec = synth.PLANE_SPHERE_160
     D = fuse_both([f], spec)[1].block_count()
     p = D - 1 if pool == "D-1" else pool
     small = synth.VolumeSpec(spec.voxel_size, spec.truncation, spec.table_slots, p)
-    gv = gpu_volume(small)
+    gv = gpu_volume(small, **MODES[mode])
     d, c = to_dev(f)
     assert gv.fuse(d, f.intr, f.pose, c) == "POOL_FULL"
     assert gv.block_count() == p
@@ -243,10 +277,11 @@ def test_pool_overflow_reported(pool):
     assert big.fuse(d, f.intr, f.pose, c) == "OK"
 
 
-def test_table_overflow_reported():
+@pytest.mark.parametrize("mode", range(len(MODES)))
+def test_table_overflow_reported(mode):
     f = synth.plane_sphere_frame()
     spec = synth.VolumeSpec(0.01, 0.04, 64, 64)
-    gv = gpu_volume(spec)
+    gv = gpu_volume(spec, **MODES[mode])
     ov = oracle_volume(spec)
     d, c = to_dev(f)
     assert ov.fuse_frame(f) == "TABLE_FULL"
@@ -254,7 +289,8 @@ def test_table_overflow_reported():
     assert gv.block_count() == 64
 
 
-def test_publish_timeout_is_bounded():
+@pytest.mark.parametrize("mode", range(len(MODES)))
+def test_publish_timeout_is_bounded(mode):
     """An entry whose key matches a block the frame needs but whose index is never
     published (Section 2.3, the publication window). The waiters give up after
     the configured limit and the call returns an error; the GPU stays usable."""
@@ -269,6 +305,8 @@ def test_publish_timeout_is_bounded():
     gv = tsdf.Volume(spec.voxel_size, spec.truncation, spec.table_slots, spec.pool_blocks,
                      memory=mem)
     assert gv.set_option("publish_timeout_ns", 20_000_000) == "OK"
+    for k, x in MODES[mode].items():
+        assert gv.set_option(k, x) == "OK"
     torch.cuda.synchronize()
     lay = gv.layout()
     slot = tsdf.tsdf_block_slot(bx, by, bz, spec.table_slots)
