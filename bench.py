@@ -81,8 +81,9 @@ class ClockSampler:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index):
+    def __init__(self, index, interval_ms=100):
         self.index = index
+        self.interval_ms = interval_ms
         self.proc = None
         self.rows = []
 
@@ -90,7 +91,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", str(self.interval_ms)],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -232,7 +233,7 @@ def run_gpu(args, rank, world, local_rank):
     torch.cuda.synchronize()
     launches0 = tsdf.tsdf_launch_count()
     points = 0
-    with ClockSampler(local_rank) as clk:
+    with ClockSampler(local_rank, args.clock_ms) as clk:
         t0 = time.perf_counter()
         for i in range(args.steps):
             points += one_step(args.warmup + i, events[i])
@@ -293,6 +294,27 @@ def run_gpu(args, rank, world, local_rank):
 
     # end to end through the public C ABI with host buffers
     e2e = run_e2e(args, vol, frames, torch, tsdf, sp, stream, flush, scrub)
+    vol.close()
+    del flush, scrub
+    torch.cuda.empty_cache()
+
+    extra = {}
+    if rank == 0 and not args.headline_only:
+        from paper_2608_08287_gb300 import serving
+        try:
+            import multiprocessing as mp
+            with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+                bank = serving.FrameBank(torch, n_frames=args.bank_frames, step=12, pool=pool)
+        except Exception as e:  # noqa: BLE001
+            bank = None
+            extra["batched"] = extra["serving"] = {"error": repr(e)}
+        if bank is not None:
+            for key, fn in (("batched", lambda: run_batched(args, torch, tsdf, serving, bank)),
+                            ("serving", lambda: run_serving(args, torch, serving, bank))):
+                try:
+                    extra[key] = fn()
+                except Exception as e:  # noqa: BLE001
+                    extra[key] = {"error": repr(e)}
 
     out = None
     if rank == 0:
@@ -311,9 +333,13 @@ def run_gpu(args, rank, world, local_rank):
                        "step_ms_p50": round(float(np.percentile(step_ms, 50)), 5),
                        "step_ms_p95": round(float(np.percentile(step_ms, 95)), 5),
                        "step_ms_p99": round(float(np.percentile(step_ms, 99)), 5),
+                       "step_ms_max": round(float(np.max(step_ms)), 5),
+                       "steps_over_2x_median": int(np.sum(np.array(step_ms) >
+                                                          2 * np.median(step_ms))),
                        "blocks_per_frame": mean("blocks"), "voxels_per_frame": mean("voxels")},
             "roofline": roof,
             "e2e": e2e,
+            **extra,
             "gpu_launches": int(launches),
             "gpu_launches_detail": "per step: the fusion kernel(s) inside the step events, plus "
                                    "1 reset kernel between steps, outside them",
@@ -354,6 +380,104 @@ def run_e2e(args, vol, frames, torch, tsdf, sp, stream, flush, scrub):
     return {"value": round(points / total, 1), "unit": UNIT,
             "h2d_bytes_per_step": W * H * 4 + W * H * 3, "d2h_bytes_per_step": 8,
             "call": "tsdf_fuse_frame_host (pinned host depth+rgb in, status word out)"}
+
+
+def run_batched(args, torch, tsdf, serving, bank):
+    """Config-4 style: 64 sessions (mixed 160x120 / 320x240 / 640x480, tables
+    2^16..2^20), one frame each per step into fresh volumes, as one batch
+    (persistent launches replayed from a CUDA graph) against a loop of
+    per-frame launches. Device time per step, L2 scrubbed between steps."""
+    from paper_2608_08287_gb300 import synth
+    n = 64
+    u = synth.uniform(20261208, 1, n)
+    res = [list(serving.SESSION_CLASSES)[int(x * 3) % 3] for x in u]
+    vols = []
+    for r in res:
+        sp = serving.SESSION_CLASSES[r]
+        vols.append(tsdf.Volume(sp.voxel_size, sp.truncation, sp.table_slots, sp.pool_blocks))
+    stream = torch.cuda.Stream()
+    sp_ = stream.cuda_stream
+    dev = []
+    for i, r in enumerate(res):
+        depth_h, rgb_h, intr, pose, pts = bank.get(r, i)
+        dev.append((depth_h.cuda(), rgb_h.cuda(), intr, pose, pts))
+    points = sum(x[4] for x in dev)
+    batch = tsdf.Batch(n, use_graph=1)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    scrub = torch.ones(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    items = [(v, d, c, intr, pose) for v, (d, c, intr, pose, _) in zip(vols, dev)]
+
+    def prep(i):
+        for v in vols:
+            v.reset(sp_)
+        with torch.cuda.stream(stream):
+            l2_scrub(flush, scrub, i)
+
+    def timed(fn, steps):
+        out = []
+        for i in range(steps):
+            prep(i)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            stream.synchronize()
+            out.append(a.elapsed_time(b))
+        return out
+
+    def batched():
+        assert batch.fuse_async(items, stream=sp_) == "OK"
+
+    def per_frame():
+        for v, d, c, intr, pose in items:
+            assert tsdf.tsdf_fuse_frame_async(v.handle, d, d.shape[1], d.shape[0], intr, pose,
+                                              c, sp_) == "OK"
+
+    timed(batched, 3)
+    tb = timed(batched, args.batch_steps)
+    st, _ = batch.status(n, stream=sp_)
+    assert st == "OK", st
+    timed(per_frame, 3)
+    tp = timed(per_frame, args.batch_steps)
+    for v in vols:
+        assert v.status(sp_) == "OK"
+        v.close()
+    batch.close()
+    mb, mp_ = float(np.mean(tb)), float(np.mean(tp))
+    return {"sessions": n, "points_per_step": int(points),
+            "batched_pts_per_s": round(points / (mb / 1e3), 1), "batched_ms_per_step": round(mb, 4),
+            "per_frame_pts_per_s": round(points / (mp_ / 1e3), 1),
+            "per_frame_ms_per_step": round(mp_, 4),
+            "launches_per_step": {"batched": 2, "per_frame": 2 * n},
+            "steps": args.batch_steps, "graph": True}
+
+
+def run_serving(args, torch, serving, bank):
+    """Config-5 style: 256 sessions, Poisson arrivals at 30 fps each, 10 s
+    window, volumes admitted by memory; continuous batching against per-frame
+    launches on the same schedule, at the nominal rate and with arrivals
+    compressed args.serve_stress times. Latency = completion - arrival."""
+    free, _ = torch.cuda.mem_get_info()
+    budget = min(0.7 * free, 200e9)
+    plans = serving.plan_sessions(args.serve_sessions, window=args.serve_window,
+                                  budget_bytes=budget)
+    admitted = [p for p in plans if len(p.arrivals)]
+    waits = np.array([p.admit - p.request for p in admitted])
+    out = {"sessions": len(plans), "window_s": args.serve_window,
+           "budget_gb": round(budget / 1e9, 1),
+           "admission_wait_ms_p50": round(float(np.percentile(waits, 50)) * 1e3, 2),
+           "admission_wait_ms_p99": round(float(np.percentile(waits, 99)) * 1e3, 2),
+           "frames_offered": int(sum(len(p.arrivals) for p in admitted))}
+    out["server"] = "tsdf_server (native continuous batching) vs one launch per frame"
+    for speed in (1.0, args.serve_stress):
+        into = out if speed == 1.0 else out.setdefault(f"stress_{speed:g}x", {})
+        for name, mode in (("batched", 0), ("per_frame", 1)):
+            res, st, _ = serving.native_replay(torch, bank, plans, mode, speed=speed)
+            torch.cuda.synchronize()
+            into[name] = res.summary()
+            into[name]["status"] = st
+    return out
 
 
 def cpu_baseline(seconds):
@@ -426,6 +550,16 @@ def main():
     ap.add_argument("--fuse-mode", type=int, default=None)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="skip the batched and serving measurements")
+    ap.add_argument("--batch-steps", type=int, default=20)
+    ap.add_argument("--clock-ms", type=int, default=100,
+                    help="nvidia-smi sampling interval during the timed region")
+    ap.add_argument("--serve-sessions", type=int, default=256)
+    ap.add_argument("--serve-window", type=float, default=10.0)
+    ap.add_argument("--serve-stress", type=float, default=3.0,
+                    help="arrival-rate multiple of the second serving run")
+    ap.add_argument("--bank-frames", type=int, default=24)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

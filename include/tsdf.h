@@ -136,7 +136,15 @@ typedef enum tsdf_option {
    * walks its points once, inserts its distinct blocks (waiting, bounded, for
    * indices published by others) and adds its sums. Results are identical up
    * to the order of floating-point additions. */
-  TSDF_OPT_FUSE_MODE = 5
+  TSDF_OPT_FUSE_MODE = 5,
+  /* Batches only: cap on resident CTAs per SM of the persistent batched
+   * kernels (0 = as many as fit, default). */
+  TSDF_OPT_CTAS_PER_SM = 6,
+  /* Batches only: 1 = capture each configuration's copy-and-launch sequence
+   * in a CUDA graph once and replay it for batches of at least 2048 tiles;
+   * smaller batches are launched directly with a grid of their own size
+   * (default 0: always launch directly). */
+  TSDF_OPT_USE_GRAPH = 7
 } tsdf_option;
 
 /* ---------------------------------------------------------------------------
@@ -251,6 +259,107 @@ tsdf_status tsdf_volume_status(tsdf_volume* vol, void* stream);
 
 /* Number of allocated blocks, min(claimed, pool_blocks). Waits for `stream`. */
 tsdf_status tsdf_volume_block_count(tsdf_volume* vol, void* stream, uint32_t* n);
+
+/* ---------------------------------------------------------------------------
+ * Batched fusion: one frame for each of many volumes (independent sessions)
+ * per launch. Not in the paper, whose harness fuses one frame per launch; the
+ * per-frame computation is the same.
+ * ------------------------------------------------------------------------- */
+
+typedef struct tsdf_batch tsdf_batch; /* opaque, owned by the library */
+
+/* One frame of a batch. All pointers as for tsdf_fuse_frame_async. */
+typedef struct tsdf_frame {
+  tsdf_volume* volume;
+  const float* depth; /* device, height x width float32 */
+  const uint8_t* rgb; /* device, height x width x 3, or NULL */
+  int width, height;
+  tsdf_intrinsics intr;
+  tsdf_pose pose;
+} tsdf_frame;
+
+/* A batch context for up to max_frames frames per call, on the current
+ * device: two session tables (device + pinned host, double-buffered) and a
+ * status buffer. */
+tsdf_status tsdf_batch_create(int max_frames, tsdf_batch** out);
+void tsdf_batch_destroy(tsdf_batch* batch);
+
+/* TSDF_OPT_PROBE_LOAD, TSDF_OPT_ALLOCATE_MODE (1 or 2), TSDF_OPT_INTEGRATE_MODE,
+ * TSDF_OPT_FUSE_MODE, TSDF_OPT_CTAS_PER_SM, TSDF_OPT_USE_GRAPH. */
+tsdf_status tsdf_batch_set_option(tsdf_batch* batch, tsdf_option opt, int64_t value);
+
+/* Enqueue the fusion of n frames (1 <= n <= max_frames), each into a distinct
+ * volume, on `stream`: allocation of every frame, then integration of every
+ * frame (two persistent launches), or one fused launch. Returns after
+ * enqueueing; it may first wait for the batch's launch before last (the
+ * session tables are double-buffered). Frame buffers must stay valid until
+ * the stream completes. Any poisoned volume rejects the whole call. */
+tsdf_status tsdf_fuse_batch_async(tsdf_batch* batch, const tsdf_frame* frames, int n,
+                                  void* stream);
+
+/* Wait for `stream` and report the status of every frame of the last batch
+ * (per_frame may be NULL; otherwise n >= that batch's size). Returns the first
+ * error found, and poisons the volumes that have one. */
+tsdf_status tsdf_batch_status(tsdf_batch* batch, void* stream, tsdf_status* per_frame, int n);
+
+/* ---------------------------------------------------------------------------
+ * Serving: continuous batching of frames from many sessions (not in the
+ * paper). A server owns device staging for its in-flight frames, a batch
+ * context and a clock; frames are submitted with their arrival times and
+ * tsdf_server_poll drives everything: it retires finished launches and, while
+ * fewer than max_inflight launches are in flight, launches the head frame of
+ * every session (volume) with nothing in flight, oldest first, up to
+ * max_batch per launch. A session's frames run in submission order.
+ * ------------------------------------------------------------------------- */
+
+typedef struct tsdf_server tsdf_server; /* opaque, owned by the library */
+
+/* One frame to serve. depth/rgb are HOST buffers (pinned for asynchronous
+ * copies) that must stay valid until the frame's completion is reported. */
+typedef struct tsdf_request {
+  tsdf_volume* volume;
+  const float* depth;   /* host, height x width float32 */
+  const uint8_t* rgb;   /* host, height x width x 3, or NULL */
+  int width, height;
+  tsdf_intrinsics intr;
+  tsdf_pose pose;
+  double arrival_s;     /* on the server's clock (replay: seconds from its start) */
+  uint64_t tag;         /* caller's identifier, returned with the completion */
+  int reset_volume;     /* 1 = empty the volume before this frame (a new session) */
+} tsdf_request;
+
+typedef struct tsdf_completion {
+  uint64_t tag;
+  double arrival_s;
+  double done_s;        /* when the server saw the frame's launch complete */
+  tsdf_status status;   /* launch status (volume errors: tsdf_volume_status) */
+} tsdf_completion;
+
+/* mode 0: continuous batching (a launch of several frames uses
+ * tsdf_fuse_batch_async, a launch of one frame the single-frame path);
+ * mode 1: one frame per launch (the baseline). max_frame_pixels bounds a
+ * frame's size; staging_frames (>= max_batch) device staging slots of that
+ * size are allocated here, and nothing is allocated afterwards. use_graph as
+ * TSDF_OPT_USE_GRAPH. All work is enqueued on `stream`. */
+tsdf_status tsdf_server_create(int mode, int max_batch, int max_inflight, int max_frame_pixels,
+                               int staging_frames, int use_graph, void* stream,
+                               tsdf_server** out);
+void tsdf_server_destroy(tsdf_server* server);
+/* Seconds since the server was created (steady clock). */
+double tsdf_server_clock(const tsdf_server* server);
+tsdf_status tsdf_server_submit(tsdf_server* server, const tsdf_request* request);
+/* Retire and launch; writes up to `capacity` completions, returns how many
+ * (-1 if server is NULL). */
+int tsdf_server_poll(tsdf_server* server, tsdf_completion* out, int capacity);
+/* Frames submitted and not yet reported complete. */
+int tsdf_server_pending(const tsdf_server* server);
+/* Replay n requests sorted by arrival (arrival_s = seconds from the start of
+ * the replay, tags unique) in real time: each is submitted when the server's
+ * clock reaches it, the loop polls until all complete, and out[i] receives
+ * request i's completion (times in seconds from the start). Returns the
+ * first launch error, else TSDF_OK. */
+tsdf_status tsdf_server_replay(tsdf_server* server, const tsdf_request* requests, int n,
+                               tsdf_completion* out);
 
 /* ---------------------------------------------------------------------------
  * Read-out (Section 2.2: means recovered at extraction)

@@ -62,6 +62,9 @@ def lib():
             L.oracle_fuse.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                       ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_void_p, ctypes.c_void_p]
+            L.oracle_export_some.restype = None
+            L.oracle_export_some.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32,
+                                             ctypes.c_void_p, ctypes.c_void_p]
             L.oracle_export.restype = ctypes.c_uint32
             L.oracle_export.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_uint32]
@@ -127,3 +130,21 @@ class OracleVolume:
             self._L.oracle_export(self._h, _ptr(coords), None if double else _ptr(vox),
                                   _ptr(vox) if double else None, n)
         return coords, vox
+
+    def export_coords(self):
+        """Block coordinates only, (n, 3) int32, ordered by coordinate."""
+        n = int(self._L.oracle_export(self._h, None, None, None, 0))
+        coords = np.zeros((n, 3), dtype=np.int32)
+        if n:
+            self._L.oracle_export(self._h, _ptr(coords), None, None, n)
+        return coords
+
+    def export_some(self, coords):
+        """(found (n,) bool, voxels (n,5,512) float64) for the given block coordinates."""
+        coords = np.ascontiguousarray(coords, dtype=np.int32).reshape(-1, 3)
+        n = len(coords)
+        vox = np.zeros((n, 5, 512), dtype=np.float64)
+        found = np.zeros(n, dtype=np.uint8)
+        if n:
+            self._L.oracle_export_some(self._h, _ptr(coords), n, _ptr(vox), _ptr(found))
+        return found.astype(bool), vox

@@ -333,4 +333,30 @@ uint32_t oracle_export(void* h, int32_t* coords, float* vox, double* vox64, uint
   return n;
 }
 
+// Export the blocks at the given coordinates (n x 3 int32), in that order, as
+// n x 5 x 512 doubles (same channels as oracle_export). found[i] = 1 if the
+// block is allocated, else 0 and its values are zero. A plain read-out.
+void oracle_export_some(void* h, const int32_t* coords, uint32_t n, double* vox64,
+                        uint8_t* found) {
+  Volume* V = static_cast<Volume*>(h);
+  for (uint32_t i = 0; i < n; ++i) {
+    const Coord c{coords[3 * i], coords[3 * i + 1], coords[3 * i + 2]};
+    auto it = V->blocks.find(c);
+    found[i] = it != V->blocks.end();
+    for (int l = 0; l < kVox; ++l) {
+      double ch[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+      if (it != V->blocks.end() && it->second.weight[l] > 0) {
+        const BlockData& B = it->second;
+        const double w = static_cast<double>(B.weight[l]);
+        ch[0] = B.tsdf_sum[l] / w;
+        ch[1] = w;
+        ch[2] = B.r_sum[l] / w;
+        ch[3] = B.g_sum[l] / w;
+        ch[4] = B.b_sum[l] / w;
+      }
+      for (int c5 = 0; c5 < 5; ++c5) vox64[(static_cast<size_t>(i) * 5 + c5) * kVox + l] = ch[c5];
+    }
+  }
+}
+
 }  // extern "C"

@@ -15,18 +15,19 @@
 
 #include "tsdf.h"
 #include "tsdf_device.cuh"
+#include "tsdf_internal.h"
 #include "tsdf_launch.h"
+
+using tsdf::align_up;
+using tsdf::as_stream;
+using tsdf::decode_err;
+using tsdf::from_cuda;
+using tsdf::kAlign;
+using tsdf::Offsets;
 
 namespace {
 
 std::atomic<uint64_t> g_launches{0};
-
-constexpr size_t kAlign = 256;
-inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
-
-struct Offsets {
-  size_t table, coords, ch[5], total;
-};
 
 bool sizes_ok(uint32_t slots, uint32_t pool) {
   return slots >= 2 && (slots & (slots - 1)) == 0 && pool >= 1 && pool <= slots;
@@ -49,33 +50,8 @@ Offsets offsets_of(uint32_t slots, uint32_t pool) {
 
 }  // namespace
 
-struct tsdf_volume {
-  int device = 0;
-  int sm_count = 0;
-  float voxel = 0.0f, trunc = 0.0f;
-  int half_band = 0;
-  uint32_t slots = 0, pool = 0;
-  void* mem = nullptr;
-  size_t bytes = 0;
-  bool owns = false;
-  Offsets off{};
-  tsdf::VolumeArgs va{};
-  bool poisoned = false;
-  uint32_t* pinned = nullptr;  // {count, err}
-  int probe_load = tsdf::kLoadCached;
-  int allocate_mode = 1;
-  int integrate_mode = 0;
-  int fuse_mode = 0;
-  int threads = 256;
-  void* stage = nullptr;
-  size_t stage_bytes = 0;
-};
-
 namespace tsdf {
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
-}  // namespace tsdf
-
-namespace {
 
 tsdf_status from_cuda(cudaError_t e) {
   if (e == cudaSuccess) return TSDF_OK;
@@ -90,8 +66,9 @@ tsdf_status decode_err(uint32_t err) {
   if (err & TSDF_ERRBIT_BOUNDS) return TSDF_ERR_BOUNDS;
   return TSDF_OK;
 }
+}  // namespace tsdf
 
-inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+namespace {
 
 // Enqueue the initialisation of an empty volume: table entries all-ones
 // (key = EMPTY, index = -1), header zero, used prefix of the pool zero.
@@ -150,9 +127,19 @@ bool params_ok(float voxel, float trunc) {
   return m >= 1 && m <= tsdf::kMaxHalfBand;
 }
 
+tsdf_status read_header(tsdf_volume* v, cudaStream_t s) {
+  cudaError_t e = cudaMemcpyAsync(v->pinned, v->mem, 2 * sizeof(uint32_t),
+                                  cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return from_cuda(e);
+}
+
+}  // namespace
+
+namespace tsdf {
 tsdf_status make_frame(const tsdf_volume* v, const float* depth, int w, int h,
                        const tsdf_intrinsics* intr, const tsdf_pose* pose, const uint8_t* rgb,
-                       tsdf::FrameArgs* f) {
+                       FrameArgs* f) {
   if (!v || !depth || !intr || !pose) return TSDF_ERR_INVALID_ARG;
   if (w < 1 || h < 1 || w > 32768 || h > 32768) return TSDF_ERR_INVALID_ARG;
   if (!(std::isfinite(intr->fx) && std::isfinite(intr->fy) && std::isfinite(intr->cx) &&
@@ -181,14 +168,9 @@ tsdf_status make_frame(const tsdf_volume* v, const float* depth, int w, int h,
   return TSDF_OK;
 }
 
-tsdf_status read_header(tsdf_volume* v, cudaStream_t s) {
-  cudaError_t e = cudaMemcpyAsync(v->pinned, v->mem, 2 * sizeof(uint32_t),
-                                  cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  return from_cuda(e);
-}
+}  // namespace tsdf
 
-}  // namespace
+using tsdf::make_frame;
 
 extern "C" {
 

@@ -1,0 +1,258 @@
+// Batched fusion: many frames, each into its own volume, in one launch per
+// stage (or one fused launch), optionally replayed from a CUDA graph.
+//
+// A batch owns two session tables (double buffering): a pinned host copy the
+// caller's frames are written into, and a device copy the kernels read. Each
+// call uses the other table, after waiting for the event recorded when that
+// table's previous launch finished, so the host prepares batch i+1 while
+// batch i runs. With graphs on, each table's copy-and-launch sequence is
+// captured once per configuration and replayed; the kernels' grids are
+// persistent, so one graph serves batches of any composition. Batches too small
+// to fill that grid are launched directly with a grid of their own size.
+#include <cstring>
+#include <new>
+
+#include <cuda_runtime.h>
+
+#include "tsdf.h"
+#include "tsdf_device.cuh"
+#include "tsdf_internal.h"
+#include "tsdf_launch.h"
+
+using tsdf::as_stream;
+using tsdf::from_cuda;
+
+struct tsdf_batch {
+  int device = 0;
+  int max_frames = 0;
+  size_t table_bytes = 0;
+  void* table_dev[2] = {nullptr, nullptr};
+  void* table_host[2] = {nullptr, nullptr};
+  cudaEvent_t done[2] = {nullptr, nullptr};
+  bool used[2] = {false, false};
+  int slot = 0;
+  int last_slot = -1;
+  int last_n = 0;
+  tsdf_volume** last_vols = nullptr;
+  unsigned* status_dev = nullptr;
+  unsigned* status_host = nullptr;
+  // configuration
+  int probe_load = 0, allocate_mode = 1, integrate_mode = 0, fuse_mode = 0, factor = 0;
+  int use_graph = 0;
+  cudaStream_t capture = nullptr;
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  long long exec_key[2] = {-1, -1};
+};
+
+namespace {
+
+long long config_key(const tsdf_batch* b) {
+  return ((((static_cast<long long>(b->probe_load) * 4 + b->allocate_mode) * 4 +
+            b->integrate_mode) * 4 + b->fuse_mode) * 64) + b->factor;
+}
+
+void drop_graphs(tsdf_batch* b) {
+  for (int i = 0; i < 2; ++i) {
+    if (b->exec[i]) cudaGraphExecDestroy(b->exec[i]);
+    b->exec[i] = nullptr;
+    b->exec_key[i] = -1;
+  }
+}
+
+cudaError_t enqueue(tsdf_batch* b, int slot, size_t bytes, int grid_limit, cudaStream_t s) {
+  cudaError_t e = cudaMemcpyAsync(b->table_dev[slot], b->table_host[slot], bytes,
+                                  cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  return tsdf::launch_batch(static_cast<const tsdf::BatchHeader*>(b->table_dev[slot]),
+                            b->probe_load, b->allocate_mode, b->integrate_mode, b->fuse_mode,
+                            b->factor, grid_limit, s);
+}
+
+// A batch smaller than this many tiles is launched directly with a grid of its
+// own size: a replayed graph's persistent grid would mostly idle.
+constexpr int kGraphMinTiles = 2048;
+
+}  // namespace
+
+extern "C" {
+
+tsdf_status tsdf_batch_create(int max_frames, tsdf_batch** out) {
+  if (!out) return TSDF_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (max_frames < 1 || max_frames > 65536) return TSDF_ERR_INVALID_ARG;
+  tsdf_batch* b = new (std::nothrow) tsdf_batch();
+  if (!b) return TSDF_ERR_OUT_OF_MEMORY;
+  b->max_frames = max_frames;
+  b->table_bytes =
+      sizeof(tsdf::BatchHeader) + static_cast<size_t>(max_frames) * sizeof(tsdf::SessionArgs);
+  cudaError_t e = cudaGetDevice(&b->device);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+    e = cudaMalloc(&b->table_dev[i], b->table_bytes);
+    if (e == cudaSuccess) e = cudaMallocHost(&b->table_host[i], b->table_bytes);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done[i], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) e = cudaMalloc(&b->status_dev, sizeof(unsigned) * max_frames);
+  if (e == cudaSuccess) e = cudaMallocHost(&b->status_host, sizeof(unsigned) * max_frames);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking);
+  b->last_vols = new (std::nothrow) tsdf_volume*[max_frames];
+  if (e != cudaSuccess || !b->last_vols) {
+    cudaGetLastError();
+    tsdf_batch_destroy(b);
+    return e == cudaErrorMemoryAllocation || e == cudaSuccess ? TSDF_ERR_OUT_OF_MEMORY
+                                                              : TSDF_ERR_CUDA;
+  }
+  *out = b;
+  return TSDF_OK;
+}
+
+void tsdf_batch_destroy(tsdf_batch* b) {
+  if (!b) return;
+  cudaDeviceSynchronize();
+  drop_graphs(b);
+  for (int i = 0; i < 2; ++i) {
+    if (b->table_dev[i]) cudaFree(b->table_dev[i]);
+    if (b->table_host[i]) cudaFreeHost(b->table_host[i]);
+    if (b->done[i]) cudaEventDestroy(b->done[i]);
+  }
+  if (b->status_dev) cudaFree(b->status_dev);
+  if (b->status_host) cudaFreeHost(b->status_host);
+  if (b->capture) cudaStreamDestroy(b->capture);
+  delete[] b->last_vols;
+  delete b;
+}
+
+tsdf_status tsdf_batch_set_option(tsdf_batch* b, tsdf_option opt, int64_t value) {
+  if (!b) return TSDF_ERR_INVALID_ARG;
+  switch (opt) {
+    case TSDF_OPT_PROBE_LOAD:
+      if (value < 0 || value > 2) return TSDF_ERR_INVALID_ARG;
+      b->probe_load = static_cast<int>(value);
+      return TSDF_OK;
+    case TSDF_OPT_ALLOCATE_MODE:
+      if (value < 1 || value > 2) return TSDF_ERR_INVALID_ARG;
+      b->allocate_mode = static_cast<int>(value);
+      return TSDF_OK;
+    case TSDF_OPT_INTEGRATE_MODE:
+      if (value < 0 || value > 1) return TSDF_ERR_INVALID_ARG;
+      b->integrate_mode = static_cast<int>(value);
+      return TSDF_OK;
+    case TSDF_OPT_FUSE_MODE:
+      if (value < 0 || value > 1) return TSDF_ERR_INVALID_ARG;
+      b->fuse_mode = static_cast<int>(value);
+      return TSDF_OK;
+    case TSDF_OPT_CTAS_PER_SM:
+      if (value < 0 || value > 32) return TSDF_ERR_INVALID_ARG;
+      b->factor = static_cast<int>(value);
+      return TSDF_OK;
+    case TSDF_OPT_USE_GRAPH:
+      if (value < 0 || value > 1) return TSDF_ERR_INVALID_ARG;
+      b->use_graph = static_cast<int>(value);
+      return TSDF_OK;
+    default:
+      return TSDF_ERR_INVALID_ARG;
+  }
+}
+
+tsdf_status tsdf_fuse_batch_async(tsdf_batch* b, const tsdf_frame* frames, int n, void* stream) {
+  if (!b || !frames || n < 1 || n > b->max_frames) return TSDF_ERR_INVALID_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != b->device) return TSDF_ERR_INVALID_ARG;
+  // validate everything before touching the table
+  for (int i = 0; i < n; ++i) {
+    tsdf_volume* v = frames[i].volume;
+    if (!v || v->device != b->device) return TSDF_ERR_INVALID_ARG;
+    for (int j = 0; j < i; ++j)
+      if (frames[j].volume == v) return TSDF_ERR_INVALID_ARG;  // one frame per volume
+    tsdf::FrameArgs f;
+    const tsdf_status st = tsdf::make_frame(v, frames[i].depth, frames[i].width,
+                                            frames[i].height, &frames[i].intr, &frames[i].pose,
+                                            frames[i].rgb, &f);
+    if (st != TSDF_OK) return st;
+    if (v->poisoned) return TSDF_ERR_POISONED;
+  }
+  const int slot = b->slot;
+  b->slot ^= 1;
+  if (b->used[slot]) {
+    const cudaError_t e = cudaEventSynchronize(b->done[slot]);
+    if (e != cudaSuccess) return from_cuda(e);
+  }
+  char* host = static_cast<char*>(b->table_host[slot]);
+  tsdf::BatchHeader* hdr = reinterpret_cast<tsdf::BatchHeader*>(host);
+  tsdf::SessionArgs* S = reinterpret_cast<tsdf::SessionArgs*>(hdr + 1);
+  int tiles = 0;
+  for (int i = 0; i < n; ++i) {
+    tsdf_volume* v = frames[i].volume;
+    tsdf::make_frame(v, frames[i].depth, frames[i].width, frames[i].height, &frames[i].intr,
+                     &frames[i].pose, frames[i].rgb, &S[i].f);
+    S[i].vol = v->va;
+    S[i].tiles_x = (frames[i].width + 15) / 16;
+    S[i].tile_begin = tiles;
+    tiles += S[i].tiles_x * ((frames[i].height + 15) / 16);
+    b->last_vols[i] = v;
+  }
+  hdr->n = n;
+  hdr->total_tiles = tiles;
+  b->last_slot = slot;
+  b->last_n = n;
+  cudaStream_t s = as_stream(stream);
+  cudaError_t e = cudaSuccess;
+  if (b->use_graph && tiles >= kGraphMinTiles) {
+    const long long key = config_key(b);
+    if (b->exec_key[slot] != key) {
+      if (b->exec[slot]) cudaGraphExecDestroy(b->exec[slot]);
+      b->exec[slot] = nullptr;
+      cudaGraph_t g = nullptr;
+      e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        // the whole table capacity is copied, so the graph serves any n
+        const cudaError_t e1 = enqueue(b, slot, b->table_bytes, 0, b->capture);
+        e = cudaStreamEndCapture(b->capture, &g);
+        if (e == cudaSuccess) e = e1;
+      }
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec[slot], g, 0);
+      if (g) cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        b->exec[slot] = nullptr;
+        return TSDF_ERR_CUDA;
+      }
+      b->exec_key[slot] = key;
+    }
+    e = cudaGraphLaunch(b->exec[slot], s);
+  } else {
+    const size_t bytes =
+        sizeof(tsdf::BatchHeader) + static_cast<size_t>(n) * sizeof(tsdf::SessionArgs);
+    e = enqueue(b, slot, bytes, tiles, s);
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(b->done[slot], s);
+  if (e != cudaSuccess) return from_cuda(e);
+  tsdf::note_launch();
+  if (b->fuse_mode == 0) tsdf::note_launch();
+  b->used[slot] = true;
+  return TSDF_OK;
+}
+
+tsdf_status tsdf_batch_status(tsdf_batch* b, void* stream, tsdf_status* per_frame, int n) {
+  if (!b || b->last_slot < 0) return TSDF_ERR_INVALID_ARG;
+  if (per_frame && n < b->last_n) return TSDF_ERR_INVALID_ARG;
+  cudaStream_t s = as_stream(stream);
+  cudaError_t e = tsdf::launch_batch_status(
+      static_cast<const tsdf::BatchHeader*>(b->table_dev[b->last_slot]), b->status_dev, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->status_host, b->status_dev, sizeof(unsigned) * b->last_n,
+                        cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return from_cuda(e);
+  tsdf_status worst = TSDF_OK;
+  for (int i = 0; i < b->last_n; ++i) {
+    const tsdf_status st = tsdf::decode_err(b->status_host[i]);
+    if (st != TSDF_OK) {
+      b->last_vols[i]->poisoned = true;
+      if (worst == TSDF_OK) worst = st;
+    }
+    if (per_frame) per_frame[i] = st;
+  }
+  return worst;
+}
+
+}  // extern "C"

@@ -88,6 +88,23 @@ struct VolumeArgs {
   unsigned long long timeout_ns;
 };
 
+// One frame of a batch: its frame and volume arguments and where its tiles
+// start in the batch's global tile numbering.
+struct SessionArgs {
+  FrameArgs f;
+  VolumeArgs vol;
+  int tiles_x;
+  int tile_begin;
+};
+static_assert(sizeof(SessionArgs) % 4 == 0, "session args are copied as words");
+
+// Header of a batch's session table in device memory; SessionArgs[n] follow.
+struct __align__(16) BatchHeader {
+  int n;
+  int total_tiles;
+  int pad[2];
+};
+
 // ----------------------------------------------------------------------------
 // geometry
 // ----------------------------------------------------------------------------

@@ -1,0 +1,57 @@
+// Internal host-side definitions shared by the host runtime files
+// (tsdf_api.cu, tsdf_batch.cu). Not part of the C ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "tsdf.h"
+#include "tsdf_device.cuh"
+
+namespace tsdf {
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+// Byte offsets of a volume's sections inside its one allocation.
+struct Offsets {
+  size_t table, coords, ch[5], total;
+};
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+tsdf_status from_cuda(cudaError_t e);
+tsdf_status decode_err(uint32_t err);
+
+}  // namespace tsdf
+
+struct tsdf_volume {
+  int device = 0;
+  int sm_count = 0;
+  float voxel = 0.0f, trunc = 0.0f;
+  int half_band = 0;
+  uint32_t slots = 0, pool = 0;
+  void* mem = nullptr;
+  size_t bytes = 0;
+  bool owns = false;
+  tsdf::Offsets off{};
+  tsdf::VolumeArgs va{};
+  bool poisoned = false;
+  uint32_t* pinned = nullptr;  // {count, err}
+  int probe_load = tsdf::kLoadCached;
+  int allocate_mode = 1;
+  int integrate_mode = 0;
+  int fuse_mode = 0;
+  int threads = 256;
+  void* stage = nullptr;
+  size_t stage_bytes = 0;
+};
+
+namespace tsdf {
+// Validate a frame and build its kernel arguments (no CUDA call).
+tsdf_status make_frame(const tsdf_volume* v, const float* depth, int w, int h,
+                       const tsdf_intrinsics* intr, const tsdf_pose* pose, const uint8_t* rgb,
+                       FrameArgs* f);
+}  // namespace tsdf

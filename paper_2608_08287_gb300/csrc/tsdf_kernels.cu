@@ -307,20 +307,22 @@ __device__ __forceinline__ void add_voxel_direct(const VolumeArgs& vol, int idx,
   }
 }
 
-// Stage A, tile strategy: one CTA per 16x16 pixel tile; the tile's distinct
-// keys are collected in the shared-memory set, then, after one barrier, the
-// list is inserted by consecutive lanes, warp-cooperatively, without waiting.
+// Stage A, tile strategy, for one 16x16 pixel tile: the tile's distinct keys
+// are collected in the shared-memory set, then, after one barrier, the list is
+// inserted by consecutive lanes, warp-cooperatively, without waiting. Every
+// thread of the CTA calls it; it ends with a barrier, so T can be reused.
 template <int P, int M>
-__global__ void __launch_bounds__(kThreads)
-    tile_allocate_kernel(const __grid_constant__ FrameArgs f,
-                         const __grid_constant__ VolumeArgs vol, int tiles_x) {
-  __shared__ TileShared T;
+__device__ __forceinline__ void tile_allocate_body(TileShared& T, const FrameArgs& f,
+                                                   const VolumeArgs& vol, int tile, int tiles_x) {
   tile_init(T, vol);
   __syncthreads();
-  if (T.err) return;  // poisoned volume: do nothing (uniform across the CTA)
+  if (T.err) {  // poisoned volume: do nothing (uniform across the CTA)
+    __syncthreads();
+    return;
+  }
   Ray r;
   int u, v;
-  const bool valid = tile_ray(f, blockIdx.x, tiles_x, r, u, v);
+  const bool valid = tile_ray(f, tile, tiles_x, r, u, v);
   Walk<M> w;
   unsigned acc;
   PointKeys pk;
@@ -333,6 +335,15 @@ __global__ void __launch_bounds__(kThreads)
     const bool has = i < n;
     warp_insert_nowait<P>(vol, has ? T.list[i] : kEmptyKey, has);
   }
+  __syncthreads();
+}
+
+template <int P, int M>
+__global__ void __launch_bounds__(kThreads)
+    tile_allocate_kernel(const __grid_constant__ FrameArgs f,
+                         const __grid_constant__ VolumeArgs vol, int tiles_x) {
+  __shared__ TileShared T;
+  tile_allocate_body<P, M>(T, f, vol, blockIdx.x, tiles_x);
 }
 
 // ----------------------------------------------------------------------------
@@ -359,17 +370,14 @@ __device__ __forceinline__ void scatter_add(const FrameArgs& f, const VolumeArgs
   }
 }
 
+// Stage B, the paper's update, for the 256 points of one tile (each thread
+// alone; no barrier).
 template <int M>
-__global__ void __launch_bounds__(kThreads)
-    integrate_scatter_kernel(const __grid_constant__ FrameArgs f,
-                             const __grid_constant__ VolumeArgs vol, int tiles_x) {
-  __shared__ unsigned int s_err;
-  if (threadIdx.x == 0) s_err = load_err_volatile(vol.hdr);
-  __syncthreads();
-  if (s_err) return;
-
+__device__ __forceinline__ void scatter_body(const FrameArgs& f, const VolumeArgs& vol, int tile,
+                                             int tiles_x) {
+  if (load_err_volatile(vol.hdr)) return;  // poisoned volume: do nothing
   int u, v;
-  tile_pixel(blockIdx.x, tiles_x, u, v);
+  tile_pixel(tile, tiles_x, u, v);
   if (u >= f.W || v >= f.H) return;
   Ray r;
   if (!make_ray(f, u, v, __ldg(f.depth + v * f.W + u), r)) return;
@@ -400,6 +408,13 @@ __global__ void __launch_bounds__(kThreads)
       scatter_add(f, vol, bc, r, gx, gy, gz, zc, colour, cr, cg, cb);
     }
   }
+}
+
+template <int M>
+__global__ void __launch_bounds__(kThreads)
+    integrate_scatter_kernel(const __grid_constant__ FrameArgs f,
+                             const __grid_constant__ VolumeArgs vol, int tiles_x) {
+  scatter_body<M>(f, vol, blockIdx.x, tiles_x);
 }
 
 // ----------------------------------------------------------------------------
@@ -490,12 +505,12 @@ __device__ __noinline__ void extra_block_voxel(const FrameArgs& f, const VolumeA
 }
 
 template <int Op, int P, int M>
-__device__ __forceinline__ void warp_body(const FrameArgs& f, const VolumeArgs& vol,
+__device__ __forceinline__ void warp_body(const FrameArgs& f, const VolumeArgs& vol, int tile,
                                           int tiles_x) {
   if (load_err_volatile(vol.hdr)) return;  // poisoned volume: do nothing
   const unsigned lane = threadIdx.x & 31u;
   int u, v;
-  tile_pixel(blockIdx.x, tiles_x, u, v);
+  tile_pixel(tile, tiles_x, u, v);
   Ray r;
   const bool valid = u < f.W && v < f.H && make_ray(f, u, v, __ldg(f.depth + v * f.W + u), r);
 
@@ -677,7 +692,7 @@ template <int Op, int P, int M, int MinBlocks>
 __global__ void __launch_bounds__(kThreads, MinBlocks)
     warp_kernel(const __grid_constant__ FrameArgs f, const __grid_constant__ VolumeArgs vol,
                 int tiles_x) {
-  warp_body<Op, P, M>(f, vol, tiles_x);
+  warp_body<Op, P, M>(f, vol, blockIdx.x, tiles_x);
 }
 
 template <int Op, int P>
@@ -701,6 +716,100 @@ static cudaError_t launch_warp_p(const FrameArgs& f, const VolumeArgs& vol, int 
     case kLoadRelaxed: return launch_warp_m<Op, kLoadRelaxed>(f, vol, s);
     default: return launch_warp_m<Op, kLoadCached>(f, vol, s);
   }
+}
+
+// ----------------------------------------------------------------------------
+// batched kernels: many frames (one per volume) in one launch
+// ----------------------------------------------------------------------------
+// The grid is persistent (a multiple of the SM count, fixed per kernel, so a
+// CUDA graph of the launch stays valid for any batch); CTAs walk the global
+// tile numbering of all frames, find each tile's frame by binary search over
+// the frames' first tiles, and run the single-frame tile body on it with the
+// frame's arguments staged in shared memory.
+__device__ __forceinline__ int find_session(const SessionArgs* S, int n, int tile) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (S[mid].tile_begin <= tile)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ void load_session(SessionArgs& dst, const SessionArgs* src) {
+  constexpr int kWords = sizeof(SessionArgs) / 4;
+  for (int i = threadIdx.x; i < kWords; i += blockDim.x)
+    reinterpret_cast<int*>(&dst)[i] = reinterpret_cast<const int*>(src)[i];
+}
+
+template <int P>
+__global__ void __launch_bounds__(kThreads)
+    batch_tile_allocate_kernel(const BatchHeader* __restrict__ table) {
+  __shared__ TileShared T;
+  __shared__ SessionArgs sa;
+  __shared__ int s_sess;
+  const int n = table->n;
+  const int total = table->total_tiles;
+  const SessionArgs* S = reinterpret_cast<const SessionArgs*>(table + 1);
+  int cur = -1;
+  for (int tile = blockIdx.x; tile < total; tile += gridDim.x) {
+    if (threadIdx.x == 0) s_sess = find_session(S, n, tile);
+    __syncthreads();
+    const int s = s_sess;
+    if (s != cur) {
+      load_session(sa, S + s);
+      cur = s;
+    }
+    __syncthreads();
+    if (sa.f.M == 4)
+      tile_allocate_body<P, 4>(T, sa.f, sa.vol, tile - sa.tile_begin, sa.tiles_x);
+    else
+      tile_allocate_body<P, 0>(T, sa.f, sa.vol, tile - sa.tile_begin, sa.tiles_x);
+  }
+}
+
+// Kind: kBatchScatter (stage B, paper's update), or a warp_body operation.
+constexpr int kBatchScatter = 10;
+
+template <int Kind, int P>
+__global__ void __launch_bounds__(kThreads) batch_point_kernel(const BatchHeader* __restrict__ table) {
+  __shared__ SessionArgs sa;
+  __shared__ int s_sess;
+  const int n = table->n;
+  const int total = table->total_tiles;
+  const SessionArgs* S = reinterpret_cast<const SessionArgs*>(table + 1);
+  int cur = -1;
+  for (int tile = blockIdx.x; tile < total; tile += gridDim.x) {
+    if (threadIdx.x == 0) s_sess = find_session(S, n, tile);
+    __syncthreads();
+    const int s = s_sess;
+    if (s != cur) {
+      load_session(sa, S + s);
+      cur = s;
+    }
+    __syncthreads();
+    const int local = tile - sa.tile_begin;
+    if constexpr (Kind == kBatchScatter) {
+      if (sa.f.M == 4)
+        scatter_body<4>(sa.f, sa.vol, local, sa.tiles_x);
+      else
+        scatter_body<0>(sa.f, sa.vol, local, sa.tiles_x);
+    } else {
+      if (sa.f.M == 4)
+        warp_body<Kind, P, 4>(sa.f, sa.vol, local, sa.tiles_x);
+      else
+        warp_body<Kind, P, 0>(sa.f, sa.vol, local, sa.tiles_x);
+    }
+    __syncthreads();  // sa and s_sess are rewritten by the next tile
+  }
+}
+
+// Each frame's sticky error word, gathered for one device-to-host copy.
+__global__ void batch_status_kernel(const BatchHeader* __restrict__ table, unsigned* out) {
+  const SessionArgs* S = reinterpret_cast<const SessionArgs*>(table + 1);
+  for (int i = threadIdx.x; i < table->n; i += blockDim.x) out[i] = load_err_volatile(S[i].vol.hdr);
 }
 
 template <int P, int M>
@@ -779,6 +888,86 @@ cudaError_t launch_fused(const FrameArgs& f, const VolumeArgs& vol, int probe_lo
   const cudaError_t e = launch_warp_p<kOpFused>(f, vol, probe_load, s);
   note_launch();
   return e;
+}
+
+// Persistent grid of a batched kernel: resident CTAs per SM x SMs, looked up
+// once per kernel (so no runtime query runs while a launch is being captured).
+template <typename K>
+static int persistent_grid(K kernel, int factor) {
+  struct Shape {
+    int sms = 0, occ = 0;
+  };
+  static Shape shape;  // one per kernel instantiation
+  if (shape.sms == 0) {
+    int dev = 0, sms = 0, occ = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kThreads, 0) != cudaSuccess)
+      return 0;
+    shape.occ = occ < 1 ? 1 : occ;
+    shape.sms = sms;
+  }
+  const int occ = (factor > 0 && factor < shape.occ) ? factor : shape.occ;
+  return occ * shape.sms;
+}
+
+template <typename K>
+static cudaError_t launch_persistent(K kernel, const BatchHeader* table, int factor,
+                                     int grid_limit, cudaStream_t s) {
+  int grid = persistent_grid(kernel, factor);
+  if (grid <= 0) return cudaErrorInvalidConfiguration;
+  if (grid_limit > 0 && grid_limit < grid) grid = grid_limit;
+  kernel<<<grid, kThreads, 0, s>>>(table);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch(const BatchHeader* table, int probe_load, int allocate_mode,
+                         int integrate_mode, int fuse_mode, int factor, int grid_limit,
+                         cudaStream_t s) {
+  cudaError_t e;
+  if (fuse_mode == 1) {
+    switch (probe_load) {
+      case kLoadL2: return launch_persistent(batch_point_kernel<kOpFused, kLoadL2>, table, factor, grid_limit, s);
+      case kLoadRelaxed:
+        return launch_persistent(batch_point_kernel<kOpFused, kLoadRelaxed>, table, factor, grid_limit, s);
+      default:
+        return launch_persistent(batch_point_kernel<kOpFused, kLoadCached>, table, factor, grid_limit, s);
+    }
+  }
+  if (allocate_mode == 2) {
+    switch (probe_load) {
+      case kLoadL2:
+        e = launch_persistent(batch_point_kernel<kOpAllocate, kLoadL2>, table, factor, grid_limit, s);
+        break;
+      case kLoadRelaxed:
+        e = launch_persistent(batch_point_kernel<kOpAllocate, kLoadRelaxed>, table, factor, grid_limit, s);
+        break;
+      default:
+        e = launch_persistent(batch_point_kernel<kOpAllocate, kLoadCached>, table, factor, grid_limit, s);
+        break;
+    }
+  } else {
+    switch (probe_load) {
+      case kLoadL2: e = launch_persistent(batch_tile_allocate_kernel<kLoadL2>, table, factor, grid_limit, s); break;
+      case kLoadRelaxed:
+        e = launch_persistent(batch_tile_allocate_kernel<kLoadRelaxed>, table, factor, grid_limit, s);
+        break;
+      default:
+        e = launch_persistent(batch_tile_allocate_kernel<kLoadCached>, table, factor, grid_limit, s);
+        break;
+    }
+  }
+  if (e != cudaSuccess) return e;
+  if (integrate_mode == 1)
+    return launch_persistent(batch_point_kernel<kOpIntegrate, kLoadCached>, table, factor, grid_limit, s);
+  return launch_persistent(batch_point_kernel<kBatchScatter, kLoadCached>, table, factor, grid_limit, s);
+}
+
+cudaError_t launch_batch_status(const BatchHeader* table, unsigned* out, cudaStream_t s) {
+  batch_status_kernel<<<1, 256, 0, s>>>(table, out);
+  note_launch();
+  return cudaGetLastError();
 }
 
 cudaError_t launch_export(const VolumeArgs& vol, float* out, unsigned int n, cudaStream_t s) {

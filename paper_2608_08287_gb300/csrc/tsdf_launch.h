@@ -17,6 +17,13 @@ cudaError_t launch_integrate(const FrameArgs& f, const VolumeArgs& vol, int mode
                              cudaStream_t s);
 cudaError_t launch_fused(const FrameArgs& f, const VolumeArgs& vol, int probe_load, int mode,
                          cudaStream_t s);
+// Batched launches (all frames of a session table): allocate + integrate, or
+// the fused kernel. factor caps the resident CTAs per SM (0 = as many as fit).
+// grid_limit > 0 caps the grid (e.g. at the batch's tile count).
+cudaError_t launch_batch(const BatchHeader* table, int probe_load, int allocate_mode,
+                         int integrate_mode, int fuse_mode, int factor, int grid_limit,
+                         cudaStream_t s);
+cudaError_t launch_batch_status(const BatchHeader* table, unsigned* out, cudaStream_t s);
 cudaError_t launch_export(const VolumeArgs& vol, float* out, unsigned int n, cudaStream_t s);
 cudaError_t launch_clear_used(const VolumeArgs& vol, int sm_count, cudaStream_t s);
 

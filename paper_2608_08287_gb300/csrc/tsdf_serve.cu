@@ -1,0 +1,273 @@
+// Native serving core: continuous batching of frames from many sessions.
+//
+// The caller submits frames (host buffers, pinned for asynchronous copies)
+// tagged with their arrival time; tsdf_server_poll drives the loop:
+//   1. every launch whose completion event has fired is retired: its frames
+//      get their completion time, their staging slots are freed;
+//   2. while fewer than max_inflight launches are in flight, the frames at the
+//      head of every session that has none in flight (oldest arrival first,
+//      at most max_batch) are copied into device staging and launched --
+//      as one batched fusion (mode 0; a batch of one frame takes the
+//      single-frame path), or one frame per launch (mode 1, the baseline).
+// Each session's frames therefore run in arrival order (one stream, at most
+// one frame of a session per launch), frames that arrive while others run join
+// the next launch, and nothing is allocated after creation.
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <deque>
+#include <new>
+#include <unordered_map>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "tsdf.h"
+#include "tsdf_internal.h"
+
+namespace {
+
+struct Pending {
+  tsdf_volume* vol;
+  const float* depth;
+  const uint8_t* rgb;
+  int w, h;
+  tsdf_intrinsics intr;
+  tsdf_pose pose;
+  double arrival;
+  uint64_t tag;
+  int reset;  // empty the volume before fusing this frame
+};
+
+struct InFlight {
+  cudaEvent_t ev;
+  std::vector<Pending> frames;
+  std::vector<int> slots;
+};
+
+}  // namespace
+
+struct tsdf_server {
+  int mode = 0;
+  int max_batch = 0, max_inflight = 0;
+  size_t slot_bytes = 0;
+  int max_pixels = 0;
+  char* staging = nullptr;
+  std::vector<int> free_slots;
+  tsdf_batch* batch = nullptr;
+  cudaStream_t stream = nullptr;
+  std::unordered_map<tsdf_volume*, std::deque<Pending>> queues;
+  std::unordered_map<tsdf_volume*, int> busy;
+  std::deque<InFlight> inflight;
+  std::vector<cudaEvent_t> events;  // free events
+  std::deque<tsdf_completion> done;
+  std::chrono::steady_clock::time_point t0;
+  int pending = 0;
+  tsdf_status sticky = TSDF_OK;
+};
+
+namespace {
+
+double now_s(const tsdf_server* s) {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now() - s->t0).count();
+}
+
+// Launch one batch (or one frame) from the queue heads. Returns false if
+// nothing was ready.
+bool launch_some(tsdf_server* s) {
+  // eligible sessions: a queued frame, nothing in flight; oldest head first
+  std::vector<std::pair<double, tsdf_volume*>> ready;
+  for (auto& kv : s->queues)
+    if (!kv.second.empty() && s->busy[kv.first] == 0)
+      ready.emplace_back(kv.second.front().arrival, kv.first);
+  if (ready.empty() || s->free_slots.empty() || s->events.empty()) return false;
+  std::sort(ready.begin(), ready.end());
+  int take = s->mode == 1 ? 1 : s->max_batch;
+  if (take > static_cast<int>(ready.size())) take = static_cast<int>(ready.size());
+  if (take > static_cast<int>(s->free_slots.size())) take = static_cast<int>(s->free_slots.size());
+  InFlight f;
+  std::vector<tsdf_frame> frames;
+  frames.reserve(take);
+  for (int i = 0; i < take; ++i) {
+    tsdf_volume* v = ready[i].second;
+    Pending p = s->queues[v].front();
+    s->queues[v].pop_front();
+    const int slot = s->free_slots.back();
+    s->free_slots.pop_back();
+    if (p.reset) {
+      const tsdf_status rs = tsdf_volume_reset(v, s->stream);
+      if (rs != TSDF_OK && s->sticky == TSDF_OK) s->sticky = rs;
+    }
+    char* dst = s->staging + static_cast<size_t>(slot) * s->slot_bytes;
+    const size_t npx = static_cast<size_t>(p.w) * p.h;
+    const size_t dbytes = tsdf::align_up(npx * sizeof(float));
+    cudaMemcpyAsync(dst, p.depth, npx * sizeof(float), cudaMemcpyHostToDevice, s->stream);
+    if (p.rgb) cudaMemcpyAsync(dst + dbytes, p.rgb, npx * 3, cudaMemcpyHostToDevice, s->stream);
+    tsdf_frame fr;
+    fr.volume = v;
+    fr.depth = reinterpret_cast<const float*>(dst);
+    fr.rgb = p.rgb ? reinterpret_cast<const uint8_t*>(dst + dbytes) : nullptr;
+    fr.width = p.w;
+    fr.height = p.h;
+    fr.intr = p.intr;
+    fr.pose = p.pose;
+    frames.push_back(fr);
+    f.frames.push_back(p);
+    f.slots.push_back(slot);
+    s->busy[v] = 1;
+  }
+  tsdf_status st;
+  if (frames.size() == 1) {
+    const tsdf_frame& fr = frames[0];
+    st = tsdf_fuse_frame_async(fr.volume, fr.depth, fr.width, fr.height, &fr.intr, &fr.pose,
+                               fr.rgb, s->stream);
+  } else {
+    st = tsdf_fuse_batch_async(s->batch, frames.data(), static_cast<int>(frames.size()),
+                               s->stream);
+  }
+  if (st != TSDF_OK && s->sticky == TSDF_OK) s->sticky = st;
+  f.ev = s->events.back();
+  s->events.pop_back();
+  cudaEventRecord(f.ev, s->stream);
+  s->inflight.push_back(std::move(f));
+  return true;
+}
+
+void retire(tsdf_server* s) {
+  while (!s->inflight.empty()) {
+    InFlight& f = s->inflight.front();
+    if (cudaEventQuery(f.ev) != cudaSuccess) break;
+    const double t = now_s(s);
+    for (size_t i = 0; i < f.frames.size(); ++i) {
+      const Pending& p = f.frames[i];
+      s->done.push_back({p.tag, p.arrival, t, s->sticky});
+      s->busy[p.vol] = 0;
+      s->free_slots.push_back(f.slots[i]);
+      --s->pending;
+    }
+    s->events.push_back(f.ev);
+    s->inflight.pop_front();
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+tsdf_status tsdf_server_create(int mode, int max_batch, int max_inflight, int max_frame_pixels,
+                               int staging_frames, int use_graph, void* stream,
+                               tsdf_server** out) {
+  if (!out) return TSDF_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (mode < 0 || mode > 1 || max_batch < 1 || max_inflight < 1 || max_inflight > 64 ||
+      max_frame_pixels < 1 || staging_frames < max_batch)
+    return TSDF_ERR_INVALID_ARG;
+  tsdf_server* s = new (std::nothrow) tsdf_server();
+  if (!s) return TSDF_ERR_OUT_OF_MEMORY;
+  s->mode = mode;
+  s->max_batch = mode == 1 ? 1 : max_batch;
+  s->max_inflight = max_inflight;
+  s->max_pixels = max_frame_pixels;
+  s->slot_bytes = tsdf::align_up(tsdf::align_up(static_cast<size_t>(max_frame_pixels) * 4) +
+                                 static_cast<size_t>(max_frame_pixels) * 3);
+  s->stream = tsdf::as_stream(stream);
+  s->t0 = std::chrono::steady_clock::now();
+  cudaError_t e = cudaMalloc(&s->staging, s->slot_bytes * staging_frames);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    delete s;
+    return TSDF_ERR_OUT_OF_MEMORY;
+  }
+  for (int i = staging_frames - 1; i >= 0; --i) s->free_slots.push_back(i);
+  for (int i = 0; i < max_inflight; ++i) {
+    cudaEvent_t ev;
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+      tsdf_server_destroy(s);
+      return TSDF_ERR_CUDA;
+    }
+    s->events.push_back(ev);
+  }
+  tsdf_status st = TSDF_OK;
+  if (mode == 0) {
+    st = tsdf_batch_create(max_batch, &s->batch);
+    if (st == TSDF_OK && use_graph) st = tsdf_batch_set_option(s->batch, TSDF_OPT_USE_GRAPH, 1);
+  }
+  if (st != TSDF_OK) {
+    tsdf_server_destroy(s);
+    return st;
+  }
+  *out = s;
+  return TSDF_OK;
+}
+
+void tsdf_server_destroy(tsdf_server* s) {
+  if (!s) return;
+  cudaStreamSynchronize(s->stream);
+  for (auto& f : s->inflight) s->events.push_back(f.ev);
+  for (cudaEvent_t ev : s->events) cudaEventDestroy(ev);
+  if (s->batch) tsdf_batch_destroy(s->batch);
+  if (s->staging) cudaFree(s->staging);
+  delete s;
+}
+
+double tsdf_server_clock(const tsdf_server* s) { return s ? now_s(s) : 0.0; }
+
+tsdf_status tsdf_server_submit(tsdf_server* s, const tsdf_request* r) {
+  if (!s || !r || !r->volume || !r->depth || r->width < 1 || r->height < 1)
+    return TSDF_ERR_INVALID_ARG;
+  if (static_cast<long long>(r->width) * r->height > s->max_pixels) return TSDF_ERR_INVALID_ARG;
+  s->queues[r->volume].push_back({r->volume, r->depth, r->rgb, r->width, r->height, r->intr,
+                                  r->pose, r->arrival_s, r->tag, r->reset_volume});
+  ++s->pending;
+  return TSDF_OK;
+}
+
+int tsdf_server_poll(tsdf_server* s, tsdf_completion* out, int capacity) {
+  if (!s) return -1;
+  retire(s);
+  while (static_cast<int>(s->inflight.size()) < s->max_inflight && launch_some(s)) {
+  }
+  int n = 0;
+  while (n < capacity && !s->done.empty()) {
+    out[n++] = s->done.front();
+    s->done.pop_front();
+  }
+  return n;
+}
+
+int tsdf_server_pending(const tsdf_server* s) { return s ? s->pending : -1; }
+
+tsdf_status tsdf_server_replay(tsdf_server* s, const tsdf_request* reqs, int n,
+                               tsdf_completion* out) {
+  if (!s || (n > 0 && (!reqs || !out))) return TSDF_ERR_INVALID_ARG;
+  for (int i = 1; i < n; ++i)
+    if (reqs[i].arrival_s < reqs[i - 1].arrival_s) return TSDF_ERR_INVALID_ARG;
+  // completions are written in request order: index requests by tag position
+  std::unordered_map<uint64_t, int> where;
+  where.reserve(static_cast<size_t>(n) * 2);
+  for (int i = 0; i < n; ++i) where[reqs[i].tag] = i;
+  if (static_cast<int>(where.size()) != n) return TSDF_ERR_INVALID_ARG;  // tags must be unique
+  const double start = now_s(s);
+  int next = 0, got = 0;
+  std::vector<tsdf_completion> buf(256);
+  while (got < n) {
+    const double t = now_s(s) - start;
+    while (next < n && reqs[next].arrival_s <= t) {
+      tsdf_request r = reqs[next++];
+      r.arrival_s += start;
+      const tsdf_status st = tsdf_server_submit(s, &r);
+      if (st != TSDF_OK) return st;
+    }
+    const int k = tsdf_server_poll(s, buf.data(), static_cast<int>(buf.size()));
+    for (int i = 0; i < k; ++i) {
+      tsdf_completion c = buf[i];
+      c.arrival_s -= start;
+      c.done_s -= start;
+      out[where[c.tag]] = c;
+    }
+    got += k;
+  }
+  return s->sticky;
+}
+
+}  // extern "C"

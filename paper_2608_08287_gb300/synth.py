@@ -16,9 +16,11 @@ Scenes (stand-ins for the paper's sphere/plane cells and TartanAir rooms,
 Section 5 and Table "cells"; the real data is not available here):
   * ``plane_sphere``: camera 1.5 m from a fronto-parallel plane with a 0.3 m
     sphere centred 1.0 m in front of the camera (160x120, fx=fy=140).
-  * ``room``: axis-aligned room (floor, ceiling, four walls) with seeded boxes
-    and spheres, depths 0.5-4 m (640x480, fx=fy=525, cx=319.5, cy=239.5),
-    seen from an orbit of radius 0.8 m around the room centre.
+  * ``room``: axis-aligned 6.4 x 2.7 x 6.4 m room (floor, ceiling, four walls)
+    with seeded boxes and spheres, depths 0.5-4 m (640x480, fx=fy=525,
+    cx=319.5, cy=239.5), seen from an orbit of radius 0.8 m around the room
+    centre whose pitch sweeps +-26 deg three times, so a full orbit sees the
+    floor and ceiling too.
 Depth noise follows the Kinect axial model of Nguyen, Izadi and Lovell
 (3DIMPVT 2012): sigma(z) = 0.0012 + 0.0019 (z - 0.4)^2 metres, Gaussian per
 pixel, followed by 5 % i.i.d. dropout to 0 (invalid).
@@ -255,6 +257,7 @@ ROOM_FLOOR = 1.2         # y down: floor at y = +1.2, ceiling at y = -1.5
 ROOM_CEIL = -1.5
 ORBIT_R = 0.8
 ORBIT_STEP_DEG = 1.2
+ORBIT_START_DEG = 0.0
 
 
 def room_prims(seed=20261204, n_boxes=6, n_spheres=4):
@@ -305,9 +308,10 @@ def orbit_pose(frame: int, seed=20261205):
     looking outward, with a seeded smooth perturbation (about 1 cm, 0.5 deg)."""
     ph = uniform(seed, 5, 8) * 2 * math.pi
     f = float(frame)
-    theta = math.radians(ORBIT_STEP_DEG) * f
+    theta = math.radians(ORBIT_START_DEG + ORBIT_STEP_DEG * f)
     yaw = theta + math.radians(0.5) * math.sin(2 * math.pi * f / 97.0 + ph[0])
-    pitch = math.radians(4.0) * math.sin(2 * math.pi * f / 131.0 + ph[1])
+    pitch = math.radians(26.0) * math.sin(2 * math.pi * f / 100.0) + \
+        math.radians(1.0) * math.sin(2 * math.pi * f / 131.0 + ph[1])
     roll = math.radians(0.5) * math.sin(2 * math.pi * f / 113.0 + ph[2])
     pos = np.array([ORBIT_R * math.sin(theta), 0.0, ORBIT_R * math.cos(theta)])
     pos = pos + 0.01 * np.array([math.sin(2 * math.pi * f / 89.0 + ph[3]),
@@ -370,7 +374,7 @@ class VolumeSpec:
 
 PLANE_SPHERE_160 = VolumeSpec(0.01, 0.04, 1 << 16, 16384)
 ROOM_640 = VolumeSpec(0.005, 0.02, 1 << 20, 1 << 18)
-ROOM_ORBIT_300 = VolumeSpec(0.005, 0.02, 1 << 16, 1 << 16)
+ROOM_ORBIT_300 = VolumeSpec(0.005, 0.02, 1 << 18, 1 << 18)   # load 0.035 -> 0.85 over the orbit
 
 
 def session_mix(n_sessions=64, seed=20261206):

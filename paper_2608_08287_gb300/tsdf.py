@@ -21,7 +21,7 @@ from .build import LIB
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OUT_OF_MEMORY", 3: "POOL_FULL", 4: "TABLE_FULL",
           5: "PUBLISH_TIMEOUT", 6: "BOUNDS", 7: "POISONED", 8: "CUDA"}
 OPTIONS = {"probe_load": 0, "publish_timeout_ns": 1, "integrate_mode": 2, "threads": 3,
-           "allocate_mode": 4, "fuse_mode": 5}
+           "allocate_mode": 4, "fuse_mode": 5, "ctas_per_sm": 6, "use_graph": 7}
 ERRBITS = {"POOL_FULL": 1, "TABLE_FULL": 2, "PUBLISH_TIMEOUT": 4, "BOUNDS": 8}
 EMPTY_KEY = 0xFFFFFFFFFFFFFFFF
 NOALLOC_MAX_PIXELS = 1 << 20
@@ -34,7 +34,11 @@ EXPORTED = ("tsdf_volume_bytes", "tsdf_volume_create", "tsdf_volume_create_in",
             "tsdf_integrate_async",
             "tsdf_volume_status", "tsdf_volume_block_count", "tsdf_export_blocks",
             "tsdf_block_key", "tsdf_block_slot", "tsdf_status_string", "tsdf_version",
-            "tsdf_launch_count")
+            "tsdf_launch_count", "tsdf_batch_create", "tsdf_batch_destroy",
+            "tsdf_batch_set_option", "tsdf_fuse_batch_async", "tsdf_batch_status",
+            "tsdf_server_create", "tsdf_server_destroy", "tsdf_server_clock",
+            "tsdf_server_submit", "tsdf_server_poll", "tsdf_server_pending",
+            "tsdf_server_replay")
 
 
 class tsdf_intrinsics(ctypes.Structure):
@@ -53,6 +57,25 @@ class tsdf_layout(ctypes.Structure):
                 ("channel", ctypes.c_void_p * 5), ("table_slots", ctypes.c_uint32),
                 ("pool_blocks", ctypes.c_uint32), ("table_offset", ctypes.c_size_t),
                 ("coords_offset", ctypes.c_size_t), ("channel_offset", ctypes.c_size_t * 5)]
+
+
+class tsdf_frame(ctypes.Structure):
+    _fields_ = [("volume", ctypes.c_void_p), ("depth", ctypes.c_void_p), ("rgb", ctypes.c_void_p),
+                ("width", ctypes.c_int), ("height", ctypes.c_int),
+                ("intr", tsdf_intrinsics), ("pose", tsdf_pose)]
+
+
+class tsdf_request(ctypes.Structure):
+    _fields_ = [("volume", ctypes.c_void_p), ("depth", ctypes.c_void_p), ("rgb", ctypes.c_void_p),
+                ("width", ctypes.c_int), ("height", ctypes.c_int),
+                ("intr", tsdf_intrinsics), ("pose", tsdf_pose),
+                ("arrival_s", ctypes.c_double), ("tag", ctypes.c_uint64),
+                ("reset_volume", ctypes.c_int)]
+
+
+class tsdf_completion(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_uint64), ("arrival_s", ctypes.c_double),
+                ("done_s", ctypes.c_double), ("status", ctypes.c_int)]
 
 
 class TsdfError(RuntimeError):
@@ -113,6 +136,21 @@ def lib() -> ctypes.CDLL:
             "tsdf_status_string": (ctypes.c_char_p, [ctypes.c_int]),
             "tsdf_version": (ctypes.c_char_p, []),
             "tsdf_launch_count": (ctypes.c_uint64, []),
+            "tsdf_batch_create": (st, [ctypes.c_int, ctypes.POINTER(_P)]),
+            "tsdf_batch_destroy": (None, [_P]),
+            "tsdf_batch_set_option": (st, [_P, ctypes.c_int, ctypes.c_int64]),
+            "tsdf_fuse_batch_async": (st, [_P, ctypes.POINTER(tsdf_frame), ctypes.c_int, _P]),
+            "tsdf_batch_status": (st, [_P, _P, ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
+            "tsdf_server_create": (st, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_int, ctypes.c_int, _P, ctypes.POINTER(_P)]),
+            "tsdf_server_destroy": (None, [_P]),
+            "tsdf_server_clock": (ctypes.c_double, [_P]),
+            "tsdf_server_submit": (st, [_P, ctypes.POINTER(tsdf_request)]),
+            "tsdf_server_poll": (ctypes.c_int, [_P, ctypes.POINTER(tsdf_completion),
+                                                ctypes.c_int]),
+            "tsdf_server_pending": (ctypes.c_int, [_P]),
+            "tsdf_server_replay": (st, [_P, ctypes.POINTER(tsdf_request), ctypes.c_int,
+                                        ctypes.POINTER(tsdf_completion)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -163,16 +201,29 @@ def _stream(s):
     return getattr(s, "cuda_stream", 0) or None
 
 
+def intrinsics(intr) -> tsdf_intrinsics:
+    """A tsdf_intrinsics struct from (fx, fy, cx, cy) (or the struct itself)."""
+    if isinstance(intr, tsdf_intrinsics):
+        return intr
+    return tsdf_intrinsics(*[float(x) for x in np.asarray(intr, dtype=np.float32).reshape(4)])
+
+
+def pose_struct(pose) -> tsdf_pose:
+    """A tsdf_pose struct from a 4x4 row-major matrix (or the struct itself)."""
+    if isinstance(pose, tsdf_pose):
+        return pose
+    p = tsdf_pose()
+    ctypes.memmove(p.m, np.ascontiguousarray(pose, dtype=np.float32).reshape(16).ctypes.data,
+                   64)
+    return p
+
+
 def _intr(intr):
-    a = [float(x) for x in np.asarray(intr, dtype=np.float32).reshape(4)]
-    return ctypes.byref(tsdf_intrinsics(*a))
+    return ctypes.byref(intrinsics(intr))
 
 
 def _pose(pose):
-    p = tsdf_pose()
-    for i, x in enumerate(np.asarray(pose, dtype=np.float32).reshape(16)):
-        p.m[i] = float(x)
-    return ctypes.byref(p)
+    return ctypes.byref(pose_struct(pose))
 
 
 def _st(code: int) -> str:
@@ -273,17 +324,18 @@ def tsdf_volume_block_count(vol, stream=None) -> int:
     return int(n.value)
 
 
-def tsdf_export_blocks(vol, stream=None):
-    """(coords int32 (n,3), voxels float32 (n,5,512)) in pool order."""
+def tsdf_export_blocks(vol, stream=None, voxels=True):
+    """(coords int32 (n,3), voxels float32 (n,5,512) or None) in pool order."""
     n = ctypes.c_uint32()
     st = _st(lib().tsdf_export_blocks(vol, None, None, 0, ctypes.byref(n), _stream(stream)))
     if st != "OK":
         raise TsdfError(st, "tsdf_export_blocks")
     coords = np.zeros((n.value, 3), dtype=np.int32)
-    vox = np.zeros((n.value, 5, 512), dtype=np.float32)
+    vox = np.zeros((n.value, 5, 512), dtype=np.float32) if voxels else None
     if n.value:
         m = ctypes.c_uint32()
-        st = _st(lib().tsdf_export_blocks(vol, coords.ctypes.data, vox.ctypes.data, n.value,
+        st = _st(lib().tsdf_export_blocks(vol, coords.ctypes.data,
+                                          vox.ctypes.data if voxels else None, n.value,
                                           ctypes.byref(m), _stream(stream)))
         if st != "OK":
             raise TsdfError(st, "tsdf_export_blocks")
@@ -308,6 +360,127 @@ def tsdf_version() -> str:
 
 def tsdf_launch_count() -> int:
     return int(lib().tsdf_launch_count())
+
+
+def tsdf_batch_create(max_frames):
+    h = _P()
+    st = _st(lib().tsdf_batch_create(max_frames, ctypes.byref(h)))
+    if st != "OK":
+        raise TsdfError(st, "tsdf_batch_create")
+    return h
+
+
+def tsdf_batch_destroy(batch) -> None:
+    lib().tsdf_batch_destroy(batch)
+
+
+def tsdf_batch_set_option(batch, option, value) -> str:
+    opt = OPTIONS[option] if isinstance(option, str) else int(option)
+    return _st(lib().tsdf_batch_set_option(batch, opt, int(value)))
+
+
+def make_frames(items):
+    """ctypes array of tsdf_frame from (volume handle, depth, rgb, intr, pose) tuples;
+    depth is a CUDA tensor (H, W) or (address, width, height)."""
+    arr = (tsdf_frame * len(items))()
+    for i, (vol, depth, rgb, intr, pose) in enumerate(items):
+        if isinstance(depth, tuple):
+            addr, w, h = depth
+        else:
+            addr, h, w = _dptr(depth), depth.shape[-2], depth.shape[-1]
+        arr[i].volume = vol.value if isinstance(vol, ctypes.c_void_p) else vol
+        arr[i].depth = addr
+        arr[i].rgb = _dptr(rgb)
+        arr[i].width = int(w)
+        arr[i].height = int(h)
+        arr[i].intr = intrinsics(intr)
+        arr[i].pose = pose_struct(pose)
+    return arr
+
+
+def tsdf_fuse_batch_async(batch, frames, n=None, stream=None) -> str:
+    n = len(frames) if n is None else n
+    return _st(lib().tsdf_fuse_batch_async(batch, frames, n, _stream(stream)))
+
+
+def tsdf_batch_status(batch, n, stream=None):
+    """(overall status, [status per frame of the last batch])."""
+    out = (ctypes.c_int * max(1, n))()
+    st = _st(lib().tsdf_batch_status(batch, _stream(stream), out, n))
+    return st, [_st(out[i]) for i in range(n)]
+
+
+def tsdf_server_create(mode, max_batch, max_inflight, max_frame_pixels, staging_frames,
+                       use_graph=1, stream=None):
+    h = _P()
+    st = _st(lib().tsdf_server_create(mode, max_batch, max_inflight, max_frame_pixels,
+                                      staging_frames, int(use_graph), _stream(stream),
+                                      ctypes.byref(h)))
+    if st != "OK":
+        raise TsdfError(st, "tsdf_server_create")
+    return h
+
+
+def tsdf_server_destroy(server) -> None:
+    lib().tsdf_server_destroy(server)
+
+
+def tsdf_server_clock(server) -> float:
+    return float(lib().tsdf_server_clock(server))
+
+
+def tsdf_server_submit(server, request) -> str:
+    return _st(lib().tsdf_server_submit(server, ctypes.byref(request)))
+
+
+def tsdf_server_poll(server, out, capacity=None) -> int:
+    return int(lib().tsdf_server_poll(server, out, len(out) if capacity is None else capacity))
+
+
+def tsdf_server_pending(server) -> int:
+    return int(lib().tsdf_server_pending(server))
+
+
+def tsdf_server_replay(server, requests, n=None):
+    """(status, completions array) for a ctypes array of tsdf_request."""
+    n = len(requests) if n is None else n
+    out = (tsdf_completion * max(1, n))()
+    st = _st(lib().tsdf_server_replay(server, requests, n, out))
+    return st, out
+
+
+class Batch:
+    """Owning wrapper around a tsdf_batch*."""
+
+    def __init__(self, max_frames, **options):
+        self.handle = tsdf_batch_create(max_frames)
+        self.max_frames = max_frames
+        for k, x in options.items():
+            if tsdf_batch_set_option(self.handle, k, x) != "OK":
+                raise ValueError(f"bad batch option {k}={x}")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            tsdf_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_option(self, option, value) -> str:
+        return tsdf_batch_set_option(self.handle, option, value)
+
+    def fuse_async(self, items, stream=None) -> str:
+        """items: (Volume, depth tensor, rgb tensor or None, intr, pose) per frame."""
+        frames = make_frames([(v.handle, d, c, i, p) for v, d, c, i, p in items])
+        self._keep = (frames, items)   # buffers stay referenced until the next call
+        return tsdf_fuse_batch_async(self.handle, frames, len(items), stream)
+
+    def status(self, n, stream=None):
+        return tsdf_batch_status(self.handle, n, stream)
 
 
 # ----------------------------------------------------------------------------
@@ -359,8 +532,8 @@ class Volume:
     def block_count(self, stream=None) -> int:
         return tsdf_volume_block_count(self.handle, stream)
 
-    def export(self, stream=None):
-        return tsdf_export_blocks(self.handle, stream)
+    def export(self, stream=None, voxels=True):
+        return tsdf_export_blocks(self.handle, stream, voxels)
 
     def set_option(self, option, value) -> str:
         return tsdf_volume_set_option(self.handle, option, value)

@@ -1,0 +1,70 @@
+"""The 300-frame orbit through the room, fused into one volume whose table
+fills up as the trajectory sees more of the room (the paper's load-factor axis,
+Section 5, taken beyond the 0.283 it could reach; Section 8 on the untested
+regime). The unbounded probe must lose no block at any load (Section 7.2): the
+GPU volume's status and block count equal the oracle's after every frame, the
+block-key set is identical, and sampled blocks agree voxel by voxel."""
+import multiprocessing as mp
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+from paper_2608_08287_gb300 import synth, tsdf
+from voxels import sort_blocks
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+def _render(i):
+    f = synth.room_frame(i)
+    return f.depth, f.rgb, f.intr, f.pose
+
+
+@pytest.fixture(scope="module")
+def frames():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2608_08287_gb300.build import build_library
+    build_library()
+    oracle.build()
+    torch.cuda.set_device(0)
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        return pool.map(_render, range(300))
+
+
+def sample_compare(gv, ov, rng, n=1500):
+    gc, gx = gv.export()
+    pick = rng.choice(len(gc), size=min(n, len(gc)), replace=False)
+    found, ox = ov.export_some(gc[pick])
+    assert found.all()
+    g = gx[pick]
+    assert np.array_equal(g[:, 1], ox[:, 1].astype(np.float32))
+    assert float(np.max(np.abs(g[:, [0, 2, 3, 4]] - ox[:, [0, 2, 3, 4]]))) <= TOL
+
+
+def test_orbit_300_frames_zero_lost_blocks(frames):
+    spec = synth.ROOM_ORBIT_300
+    gv = tsdf.Volume(spec.voxel_size, spec.truncation, spec.table_slots, spec.pool_blocks)
+    ov = oracle.OracleVolume(spec.voxel_size, spec.truncation, spec.table_slots,
+                             spec.pool_blocks)
+    rng = np.random.default_rng(1)
+    loads = []
+    for i, (depth, rgb, intr, pose) in enumerate(frames):
+        d = torch.from_numpy(depth).cuda()
+        c = torch.from_numpy(rgb).cuda()
+        sg = gv.fuse(d, intr, pose, c)
+        so = ov.fuse(depth, intr, pose, rgb)
+        assert sg == so == "OK", (i, sg, so)
+        n = gv.block_count()
+        assert n == ov.block_count(), i          # zero lost blocks, every frame
+        loads.append(n / spec.table_slots)
+        if i in (99, 299):
+            gc, _ = gv.export(voxels=False)
+            assert np.array_equal(sort_blocks(gc, np.zeros((len(gc), 1)))[0], ov.export_coords())
+            sample_compare(gv, ov, rng)
+    assert loads[0] < 0.1 and loads[-1] > 0.8, (loads[0], loads[-1])
