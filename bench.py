@@ -68,9 +68,31 @@ def l2_scrub(flush, scrub, i):
     scrub.sum()
 
 
+def frame_indices(rank=0):
+    """Orbit frames that rank `rank` fuses: every rank a distinct set (replicas
+    of the path on different inputs, no data exchanged)."""
+    return [37 * (rank * N_FRAMES + i) for i in range(N_FRAMES)]
+
+
 def make_frames(rank=0):
     from paper_2608_08287_gb300 import synth
-    return [synth.room_frame(37 * (rank * N_FRAMES + i)) for i in range(N_FRAMES)]
+    return [synth.room_frame(k) for k in frame_indices(rank)]
+
+
+def reduce_job(points, elapsed, world, device):
+    """Whole-job totals over the ranks: points summed, elapsed time the maximum
+    (the job ends with its slowest rank). The only collective on the bench
+    path; it runs outside the timed region. `device` is "cuda" under NCCL,
+    "cpu" under gloo."""
+    if world <= 1:
+        return int(points), float(elapsed)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(elapsed)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    p = torch.tensor([int(points)], device=device, dtype=torch.int64)
+    dist.all_reduce(p)
+    return int(p.item()), float(t.item())
 
 
 # ----------------------------------------------------------------------------
@@ -246,16 +268,7 @@ def run_gpu(args, rank, world, local_rank):
     st = vol.status(sp)
     assert st == "OK", st
     step_ms = [events[i][0].elapsed_time(events[i][1]) for i in range(args.steps)]
-    total_ms = float(sum(step_ms))
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-        pts = torch.tensor([points], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(pts)
-        points_all = int(pts.item())
-    else:
-        points_all = points
+    points_all, total_ms = reduce_job(points, float(sum(step_ms)), world, "cuda")
     value = points_all / (total_ms / 1e3)
 
     # the two-stage split of the same frames, for the per-stage rooflines
@@ -293,7 +306,7 @@ def run_gpu(args, rank, world, local_rank):
             "traffic": committed_traffic(dom[4])}
 
     # end to end through the public C ABI with host buffers
-    e2e = run_e2e(args, vol, frames, torch, tsdf, sp, stream, flush, scrub)
+    e2e = run_e2e(args, vol, frames, torch, tsdf, sp, stream, flush, scrub, world)
     vol.close()
     del flush, scrub
     torch.cuda.empty_cache()
@@ -305,8 +318,11 @@ def run_gpu(args, rank, world, local_rank):
             import multiprocessing as mp
             with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
                 bank = serving.FrameBank(torch, n_frames=args.bank_frames, step=12, pool=pool)
+                sweep_frames = (pool.starmap(serving._render,
+                                             [(640, 480, k) for k in range(args.sweep_frames)])
+                                if args.sweep_frames else None)
         except Exception as e:  # noqa: BLE001
-            bank = None
+            bank = sweep_frames = None
             extra["batched"] = extra["serving"] = {"error": repr(e)}
         if bank is not None:
             for key, fn in (("batched", lambda: run_batched(args, torch, tsdf, serving, bank)),
@@ -315,6 +331,11 @@ def run_gpu(args, rank, world, local_rank):
                     extra[key] = fn()
                 except Exception as e:  # noqa: BLE001
                     extra[key] = {"error": repr(e)}
+        if sweep_frames:
+            try:
+                extra["load_sweep"] = run_load_sweep(args, torch, tsdf, sweep_frames)
+            except Exception as e:  # noqa: BLE001
+                extra["load_sweep"] = {"error": repr(e)}
 
     out = None
     if rank == 0:
@@ -352,7 +373,7 @@ def run_gpu(args, rank, world, local_rank):
     return out
 
 
-def run_e2e(args, vol, frames, torch, tsdf, sp, stream, flush, scrub):
+def run_e2e(args, vol, frames, torch, tsdf, sp, stream, flush, scrub, world=1):
     """Same metric through tsdf_fuse_frame_host: pinned host depth + colour are
     copied in, both stages run, the status word is read back, every step."""
     host = [(torch.from_numpy(f.depth).pin_memory(), torch.from_numpy(f.rgb).pin_memory())
@@ -377,6 +398,7 @@ def run_e2e(args, vol, frames, torch, tsdf, sp, stream, flush, scrub):
         total += time.perf_counter() - t0
         assert st == "OK", st
         points += f.valid_points
+    points, total = reduce_job(points, total, world, "cuda")
     return {"value": round(points / total, 1), "unit": UNIT,
             "h2d_bytes_per_step": W * H * 4 + W * H * 3, "d2h_bytes_per_step": 8,
             "call": "tsdf_fuse_frame_host (pinned host depth+rgb in, status word out)"}
@@ -480,6 +502,120 @@ def run_serving(args, torch, serving, bank):
     return out
 
 
+SWEEP_LOADS = (0.1, 0.3, 0.5, 0.7, 0.9)
+SWEEP_SLOTS = 1 << 17
+SWEEP_BOUND = 8        # the trip count of the printed bounded probe (Section 7)
+
+
+def run_load_sweep(args, torch, tsdf, rendered):
+    """Load-factor sweep up to 0.9 with the table decoupled from the block
+    count (Section 8's open question: where probe chains really lengthen).
+    The room orbit (640x480, 5 mm voxels, 2 cm truncation) is fused frame by
+    frame into a volume whose table and pool both hold 2^17 blocks. When the
+    load first passes each target, the volume is snapshotted and the NEXT
+    frame's fusion is timed from that snapshot (restored before every
+    repetition, outside the events; L2 scrubbed) for each strategy, beside
+    the table's probe lengths and what a probe bounded at 8 (fed the same
+    frames from the start) has silently lost by then."""
+    from paper_2608_08287_gb300 import synth
+    spec = synth.VolumeSpec(0.005, 0.02, SWEEP_SLOTS, SWEEP_SLOTS)
+    stream = torch.cuda.Stream()
+    sp = stream.cuda_stream
+    frames = [(torch.from_numpy(d).cuda(), torch.from_numpy(c).cuda(), tsdf.intrinsics(i),
+               tsdf.pose_struct(p), int(np.count_nonzero(d > 0))) for d, c, i, p in rendered]
+
+    def vol(**opts):
+        v = tsdf.Volume(spec.voxel_size, spec.truncation, spec.table_slots, spec.pool_blocks)
+        for k, x in opts.items():
+            assert v.set_option(k, x) == "OK"
+        return v
+
+    fill, snap, work = vol(), vol(), vol()
+    kfill, ksnap, kwork = vol(slot_index=1), vol(slot_index=1), vol(slot_index=1)
+    bfill = vol(probe_bound=SWEEP_BOUND, allocate_mode=0, integrate_mode=0)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    scrub = torch.ones(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    variants = (("tile+scatter", work, snap, dict(allocate_mode=1, integrate_mode=0, fuse_mode=0)),
+                ("paper_protocol", work, snap, dict(allocate_mode=0, integrate_mode=0, fuse_mode=0)),
+                ("fused_warp", work, snap, dict(fuse_mode=1)),
+                ("slot_index", kwork, ksnap, dict(allocate_mode=1, integrate_mode=0, fuse_mode=0)))
+
+    def fuse(v, fr):
+        d, c, intr, pose, _ = fr
+        assert tsdf.tsdf_fuse_frame_async(v.handle, d, 640, 480, intr, pose, c, sp) == "OK"
+
+    def time_next(name, w, src, opts, fr):
+        for k, x in opts.items():
+            assert w.set_option(k, x) == "OK"
+        d, c, intr, pose, _ = fr
+        ta, tb = [], []
+        for r in range(3 + args.sweep_reps):
+            assert w.copy_from(src, sp) == "OK"
+            with torch.cuda.stream(stream):
+                l2_scrub(flush, scrub, r)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            ev[0].record(stream)
+            if opts.get("fuse_mode", 0):
+                assert tsdf.tsdf_fuse_frame_async(w.handle, d, 640, 480, intr, pose, c, sp) == "OK"
+                ev[1].record(stream)
+            else:
+                assert tsdf.tsdf_allocate_async(w.handle, d, 640, 480, intr, pose, sp) == "OK"
+                ev[1].record(stream)
+                assert tsdf.tsdf_integrate_async(w.handle, d, 640, 480, intr, pose, c, sp) == "OK"
+            ev[2].record(stream)
+            stream.synchronize()
+            if r >= 3:
+                ta.append(ev[0].elapsed_time(ev[1]))
+                tb.append(ev[1].elapsed_time(ev[2]))
+        assert w.status(sp) == "OK", name
+        total = float(np.median(np.add(ta, tb)))
+        out = {"ms": round(total, 4), "pts_per_s": round(fr[4] / (total / 1e3), 1),
+               "blocks_after": w.block_count(sp)}
+        if not opts.get("fuse_mode", 0):
+            out["allocate_ms"] = round(float(np.median(ta)), 4)
+            out["integrate_ms"] = round(float(np.median(tb)), 4)
+        return out
+
+    points = []
+    targets = list(SWEEP_LOADS)
+    for k in range(len(frames) - 1):
+        if not targets:
+            break
+        for v in (fill, kfill, bfill):
+            fuse(v, frames[k])
+        n = fill.block_count(sp)
+        if n < targets[0] * SWEEP_SLOTS:
+            continue
+        while targets and n >= targets[0] * SWEEP_SLOTS:
+            targets.pop(0)
+        assert fill.status(sp) == kfill.status(sp) == bfill.status(sp) == "OK"
+        st, bst = fill.table_stats(sp), bfill.table_stats(sp)
+        assert kfill.block_count(sp) == n
+        assert snap.copy_from(fill, sp) == "OK" and ksnap.copy_from(kfill, sp) == "OK"
+        row = {"frame": k, "blocks": n, "load": round(n / SWEEP_SLOTS, 4),
+               "probe_mean": round(st["probe_sum"] / max(1, st["occupied_slots"]), 2),
+               "probe_max": st["probe_max"],
+               f"bounded{SWEEP_BOUND}": {
+                   "status": bfill.status(sp),
+                   "blocks_lost": n - bst["blocks"],
+                   "contributions_lost": st["weight_sum"] - bst["weight_sum"],
+                   "contributions": st["weight_sum"]},
+               "next_frame_points": frames[k + 1][4]}
+        timings = {name: time_next(name, w, src, opts, frames[k + 1])
+                   for name, w, src, opts in variants}
+        after = {t["blocks_after"] for t in timings.values()}
+        assert len(after) == 1, timings   # every strategy allocates the same blocks
+        row["timings"] = timings
+        points.append(row)
+    for v in (fill, snap, work, kfill, ksnap, kwork, bfill):
+        v.close()
+    return {"workload": "room orbit 640x480, voxel 5 mm, truncation 2 cm, "
+                        "table 2^17 slots, pool 2^17 blocks",
+            "timed": "fusion of the frame after the checkpoint, from a restored snapshot, "
+                     f"median of {args.sweep_reps}, L2 scrubbed",
+            "points": points}
+
+
 def cpu_baseline(seconds):
     """The oracle as it stands, single-threaded on a host core, on whole frames."""
     import oracle
@@ -560,6 +696,9 @@ def main():
     ap.add_argument("--serve-stress", type=float, default=3.0,
                     help="arrival-rate multiple of the second serving run")
     ap.add_argument("--bank-frames", type=int, default=24)
+    ap.add_argument("--sweep-frames", type=int, default=142,
+                    help="orbit frames rendered for the load-factor sweep (0 = no sweep)")
+    ap.add_argument("--sweep-reps", type=int, default=10)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

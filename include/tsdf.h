@@ -85,7 +85,7 @@ typedef struct tsdf_layout {
   uint32_t* block_count;   /* device: blocks claimed (may exceed pool on overflow) */
   uint32_t* error_word;    /* device: sticky error bits, see TSDF_ERRBIT_* */
   void* table;             /* device: table_slots entries {uint64 key; int32 idx; int32 pad} */
-  int32_t* block_coords;   /* device: pool_blocks x {bx, by, bz} */
+  int32_t* block_coords;   /* device: pool_blocks x {bx, by, bz} (unused with TSDF_OPT_SLOT_INDEX) */
   float* channel[5];       /* device: tsdf sum, weight, red sum, green sum, blue sum */
   uint32_t table_slots;
   uint32_t pool_blocks;
@@ -144,7 +144,24 @@ typedef enum tsdf_option {
    * in a CUDA graph once and replay it for batches of at least 2048 tiles;
    * smaller batches are launched directly with a grid of their own size
    * (default 0: always launch directly). */
-  TSDF_OPT_USE_GRAPH = 7
+  TSDF_OPT_USE_GRAPH = 7,
+  /* 1 = a block's pool index is its table slot (Section 6, "Deriving the
+   * location from the slot"): the slot winner only counts the block, a thread
+   * that finds its key has the index at once, nothing is published and no
+   * thread waits. Requires pool_blocks == table_slots (the pool is sized to
+   * the table) and a volume with nothing fused since creation or the last
+   * reset; TSDF_ERR_INVALID_ARG otherwise. The block_coords array is then
+   * unused (the key holds the coordinate) and tsdf_export_blocks returns the
+   * blocks in slot order. Overflow can only be TSDF_ERR_TABLE_FULL.
+   * 0 = counter-assigned indices (default). */
+  TSDF_OPT_SLOT_INDEX = 8,
+  /* NEGATIVE CONTROL, never for real use: 0 = unbounded probe (default);
+   * B > 0 = every insert and lookup gives up after B probes WITHOUT reporting
+   * it, so blocks and contributions can be lost silently -- the behaviour of a
+   * probe loop with a compile-time trip count (Section 7, the bounded probe
+   * of the Triton arm). It exists to measure that loss against the unbounded
+   * probe. Values above table_slots act as unbounded. */
+  TSDF_OPT_PROBE_BOUND = 9
 } tsdf_option;
 
 /* ---------------------------------------------------------------------------
@@ -365,7 +382,8 @@ tsdf_status tsdf_server_replay(tsdf_server* server, const tsdf_request* requests
  * Read-out (Section 2.2: means recovered at extraction)
  * ------------------------------------------------------------------------- */
 
-/* Copy every allocated block to host memory, in pool order: coords_host gets
+/* Copy every allocated block to host memory, in pool order (slot order with
+ * TSDF_OPT_SLOT_INDEX): coords_host gets
  * n x {bx, by, bz}; voxels_host gets n x 5 x 512 float32, per block the
  * channels {tsdf mean, weight, red mean, green mean, blue mean} (means are
  * sum / weight where weight > 0, else 0; colours in [0, 1]). If capacity < n
@@ -373,6 +391,30 @@ tsdf_status tsdf_server_replay(tsdf_server* server, const tsdf_request* requests
  * Either host pointer may be NULL to query n. Waits for `stream`. */
 tsdf_status tsdf_export_blocks(tsdf_volume* vol, int32_t* coords_host, float* voxels_host,
                                uint32_t capacity, uint32_t* n_out, void* stream);
+
+/* Diagnostics of a volume's table and pool (a read-out, not part of fusion).
+ * A key's probe length is its distance from its home slot plus one: the
+ * number of entries an unbounded probe reads to find it (Section 3.1, linear
+ * probing). weight_sum is the sum of every voxel weight, i.e. the number of
+ * contributions the volume has received (weights are 1 per contribution). */
+typedef struct tsdf_table_stats {
+  uint64_t occupied_slots; /* entries holding a key */
+  uint64_t probe_sum;      /* sum of the keys' probe lengths */
+  uint32_t probe_max;      /* longest probe length (0 when empty) */
+  uint32_t blocks;         /* min(claimed, pool_blocks), as tsdf_volume_block_count */
+  uint64_t weight_sum;     /* sum of all voxel weights of the allocated blocks */
+} tsdf_table_stats;
+
+/* Fill *out for `vol`. Enqueues two kernels on `stream` and waits for it. */
+tsdf_status tsdf_volume_table_stats(tsdf_volume* vol, void* stream, tsdf_table_stats* out);
+
+/* Copy the whole state of `src` (header, table, coordinates, pool, poisoned
+ * flag) into `dst`, device to device on `stream` (not waited for). Both must
+ * have the same voxel size, truncation, table_slots, pool_blocks and
+ * TSDF_OPT_SLOT_INDEX setting and live on the current device; options other
+ * than the slot index are not copied. For snapshots and restores (e.g. timing
+ * a fusion repeatedly from the same state). */
+tsdf_status tsdf_volume_copy(tsdf_volume* dst, const tsdf_volume* src, void* stream);
 
 /* ---------------------------------------------------------------------------
  * Exact integer helpers (the device code uses the same definitions)

@@ -112,6 +112,8 @@ tsdf_status init_volume(tsdf_volume* v, void* mem, size_t bytes, bool owns, floa
   v->va.pool = pool;
   for (int c = 0; c < 5; ++c) v->va.ch[c] = reinterpret_cast<float*>(base + v->off.ch[c]);
   v->va.timeout_ns = 1000000000ull;
+  v->va.probe_limit = slots;
+  v->va.slot_index = 0;
   e = cudaMallocHost(reinterpret_cast<void**>(&v->pinned), 2 * sizeof(uint32_t));
   if (e != cudaSuccess) {
     v->pinned = nullptr;
@@ -233,7 +235,10 @@ tsdf_status tsdf_volume_create_in(void* dev_mem, size_t bytes, float voxel_size,
 tsdf_status tsdf_volume_reset(tsdf_volume* vol, void* stream) {
   if (!vol) return TSDF_ERR_INVALID_ARG;
   const tsdf_status st = enqueue_clear(vol, as_stream(stream), false);
-  if (st == TSDF_OK) vol->poisoned = false;
+  if (st == TSDF_OK) {
+    vol->poisoned = false;
+    vol->dirty = false;
+  }
   return st;
 }
 
@@ -273,6 +278,21 @@ tsdf_status tsdf_volume_set_option(tsdf_volume* vol, tsdf_option opt, int64_t va
       if (value < 0 || value > 1) return TSDF_ERR_INVALID_ARG;
       vol->fuse_mode = static_cast<int>(value);
       return TSDF_OK;
+    case TSDF_OPT_SLOT_INDEX:
+      if (value < 0 || value > 1) return TSDF_ERR_INVALID_ARG;
+      if (value == 1 && vol->pool != vol->slots) return TSDF_ERR_INVALID_ARG;
+      if (vol->dirty && static_cast<unsigned int>(value) != vol->va.slot_index)
+        return TSDF_ERR_INVALID_ARG;  // the layout of the stored blocks would change
+      vol->va.slot_index = static_cast<unsigned int>(value);
+      return TSDF_OK;
+    case TSDF_OPT_PROBE_BOUND:
+      if (value < 0) return TSDF_ERR_INVALID_ARG;
+      vol->va.probe_limit = (value == 0 || value >= static_cast<int64_t>(vol->slots))
+                                ? vol->slots
+                                : static_cast<unsigned int>(value);
+      return TSDF_OK;
+    default:
+      break;
   }
   return TSDF_ERR_INVALID_ARG;
 }
@@ -304,6 +324,7 @@ tsdf_status tsdf_allocate_async(tsdf_volume* vol, const float* depth_dev, int wi
   tsdf_status st = make_frame(vol, depth_dev, width, height, intr, pose, nullptr, &f);
   if (st != TSDF_OK) return st;
   if (vol->poisoned) return TSDF_ERR_POISONED;
+  vol->dirty = true;
   return from_cuda(tsdf::launch_allocate(f, vol->va, vol->probe_load, vol->allocate_mode, as_stream(stream)));
 }
 
@@ -315,6 +336,7 @@ tsdf_status tsdf_integrate_async(tsdf_volume* vol, const float* depth_dev, int w
   tsdf_status st = make_frame(vol, depth_dev, width, height, intr, pose, rgb_dev, &f);
   if (st != TSDF_OK) return st;
   if (vol->poisoned) return TSDF_ERR_POISONED;
+  vol->dirty = true;
   return from_cuda(tsdf::launch_integrate(f, vol->va, vol->integrate_mode, as_stream(stream)));
 }
 
@@ -326,6 +348,7 @@ tsdf_status tsdf_fuse_frame_async(tsdf_volume* vol, const float* depth_dev, int 
   tsdf_status st = make_frame(vol, depth_dev, width, height, intr, pose, rgb_dev, &f);
   if (st != TSDF_OK) return st;
   if (vol->poisoned) return TSDF_ERR_POISONED;
+  vol->dirty = true;
   if (vol->fuse_mode != 0)
     return from_cuda(
         tsdf::launch_fused(f, vol->va, vol->probe_load, vol->fuse_mode, as_stream(stream)));
@@ -410,22 +433,85 @@ tsdf_status tsdf_export_blocks(tsdf_volume* vol, int32_t* coords_host, float* vo
   if (capacity < n) return TSDF_ERR_INVALID_ARG;
   if (n == 0) return TSDF_OK;
   cudaError_t e = cudaSuccess;
-  if (coords_host)
-    e = cudaMemcpyAsync(coords_host, vol->va.coords, static_cast<size_t>(n) * 3 * sizeof(int32_t),
+  const int32_t* coords_dev = vol->va.coords;
+  const unsigned int* list = nullptr;
+  char* scratch = nullptr;
+  if (vol->va.slot_index) {
+    // the blocks sit at their slots: list the occupied slots first
+    const size_t list_bytes = align_up(static_cast<size_t>(n) * sizeof(unsigned int));
+    const size_t coord_bytes = align_up(static_cast<size_t>(n) * 3 * sizeof(int32_t));
+    e = cudaMallocAsync(reinterpret_cast<void**>(&scratch), list_bytes + coord_bytes + kAlign, s);
+    if (e == cudaSuccess) {
+      list = reinterpret_cast<const unsigned int*>(scratch);
+      coords_dev = reinterpret_cast<const int32_t*>(scratch + list_bytes);
+      e = tsdf::launch_slot_list(vol->va, reinterpret_cast<unsigned int*>(scratch),
+                                 reinterpret_cast<int32_t*>(scratch + list_bytes), n,
+                                 reinterpret_cast<unsigned int*>(scratch + list_bytes +
+                                                                 coord_bytes),
+                                 s);
+    }
+  }
+  if (e == cudaSuccess && coords_host)
+    e = cudaMemcpyAsync(coords_host, coords_dev, static_cast<size_t>(n) * 3 * sizeof(int32_t),
                         cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess && voxels_host) {
     const size_t bytes = static_cast<size_t>(n) * 5 * tsdf::kBlockVoxels * sizeof(float);
     float* tmp = nullptr;
     e = cudaMallocAsync(reinterpret_cast<void**>(&tmp), bytes, s);
     if (e == cudaSuccess) {
-      e = tsdf::launch_export(vol->va, tmp, n, s);
+      e = tsdf::launch_export(vol->va, tmp, n, list, s);
       if (e == cudaSuccess) e = cudaMemcpyAsync(voxels_host, tmp, bytes, cudaMemcpyDeviceToHost, s);
       const cudaError_t e2 = cudaFreeAsync(tmp, s);
       if (e == cudaSuccess) e = e2;
     }
   }
+  if (scratch) {
+    const cudaError_t e2 = cudaFreeAsync(scratch, s);
+    if (e == cudaSuccess) e = e2;
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   return from_cuda(e);
+}
+
+tsdf_status tsdf_volume_table_stats(tsdf_volume* vol, void* stream, tsdf_table_stats* out) {
+  if (!vol || !out) return TSDF_ERR_INVALID_ARG;
+  cudaStream_t s = as_stream(stream);
+  tsdf::TableStatsDev* dev = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&dev), sizeof(*dev), s);
+  if (e != cudaSuccess) return from_cuda(e);
+  tsdf::TableStatsDev host{};
+  e = cudaMemsetAsync(dev, 0, sizeof(*dev), s);
+  if (e == cudaSuccess) e = tsdf::launch_table_stats(vol->va, dev, vol->sm_count, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&host, dev, sizeof(host), cudaMemcpyDeviceToHost, s);
+  const cudaError_t e2 = cudaFreeAsync(dev, s);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return from_cuda(e);
+  uint32_t n = 0;
+  const tsdf_status st = tsdf_volume_block_count(vol, stream, &n);
+  if (st != TSDF_OK) return st;
+  out->occupied_slots = host.occupied;
+  out->probe_sum = host.probe_sum;
+  out->probe_max = host.probe_max;
+  out->blocks = n;
+  out->weight_sum = host.weight_sum;
+  return TSDF_OK;
+}
+
+tsdf_status tsdf_volume_copy(tsdf_volume* dst, const tsdf_volume* src, void* stream) {
+  if (!dst || !src || dst == src) return TSDF_ERR_INVALID_ARG;
+  if (dst->slots != src->slots || dst->pool != src->pool || dst->voxel != src->voxel ||
+      dst->trunc != src->trunc || dst->device != src->device ||
+      dst->va.slot_index != src->va.slot_index)
+    return TSDF_ERR_INVALID_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != dst->device) return TSDF_ERR_INVALID_ARG;
+  const cudaError_t e = cudaMemcpyAsync(dst->mem, src->mem, src->off.total,
+                                        cudaMemcpyDeviceToDevice, as_stream(stream));
+  if (e != cudaSuccess) return from_cuda(e);
+  dst->poisoned = src->poisoned;
+  dst->dirty = src->dirty;
+  return TSDF_OK;
 }
 
 uint64_t tsdf_block_key(int32_t bx, int32_t by, int32_t bz) {

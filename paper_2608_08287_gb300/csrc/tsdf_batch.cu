@@ -185,6 +185,7 @@ tsdf_status tsdf_fuse_batch_async(tsdf_batch* b, const tsdf_frame* frames, int n
     tsdf::make_frame(v, frames[i].depth, frames[i].width, frames[i].height, &frames[i].intr,
                      &frames[i].pose, frames[i].rgb, &S[i].f);
     S[i].vol = v->va;
+    v->dirty = true;
     S[i].tiles_x = (frames[i].width + 15) / 16;
     S[i].tile_begin = tiles;
     tiles += S[i].tiles_x * ((frames[i].height + 15) / 16);

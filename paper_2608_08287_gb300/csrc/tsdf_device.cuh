@@ -86,6 +86,24 @@ struct VolumeArgs {
   float* ch[5];            // tsdf sum, weight, r sum, g sum, b sum
   Header* hdr;
   unsigned long long timeout_ns;
+  // Probes before a scan gives up: table_slots (unbounded in the paper's
+  // sense: a full scan reports TABLE_FULL), or a smaller bound that gives up
+  // SILENTLY -- the negative control of a bounded probe (Section 7), never a
+  // default.
+  unsigned int probe_limit;
+  // Nonzero: a block's pool index is its table slot (Section 6, "Deriving the
+  // location from the slot"); pool == table_slots, no index is published and
+  // no thread waits.
+  unsigned int slot_index;
+};
+
+// Diagnostic read-out of a volume (tsdf_volume_table_stats).
+struct TableStatsDev {
+  unsigned long long occupied;    // table entries holding a key
+  unsigned long long probe_sum;   // sum over keys of (distance from home slot + 1)
+  unsigned long long weight_sum;  // sum of voxel weights over the used blocks
+  unsigned int probe_max;
+  unsigned int pad;
 };
 
 // One frame of a batch: its frame and volume arguments and where its tiles
@@ -320,6 +338,17 @@ static __device__ __noinline__ int wait_published(const VolumeArgs& vol, const E
   return -1;
 }
 
+__device__ __forceinline__ void red_add_u32(unsigned int* p, unsigned int v) {
+  asm volatile("red.relaxed.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// A scan that ran out of probes: with the unbounded probe that means every
+// slot was visited, which is reported; a bounded probe (negative control)
+// gives up without a trace.
+__device__ __forceinline__ void probe_exhausted(const VolumeArgs& vol) {
+  if (vol.probe_limit >= vol.slots) atomicOr(&vol.hdr->err, TSDF_ERRBIT_TABLE_FULL);
+}
+
 // Insert protocol of Listing 1 (Section 2.3): linear probe from the home slot;
 // a plain load of the entry; on EMPTY a 64-bit compare-exchange; the winner
 // takes a pool index from the counter, writes the block coordinate, fences and
@@ -327,7 +356,11 @@ static __device__ __noinline__ int wait_published(const VolumeArgs& vol, const E
 // After a lost exchange the slot is re-examined with the key that won it (a
 // set slot never changes, so if it holds our key this is a hit; moving on
 // would duplicate the key). The scan is bounded only by the table size; a full
-// scan reports TABLE_FULL. Returns the pool index or -1 on error.
+// scan reports TABLE_FULL (vol.probe_limit may lower the bound for the
+// negative control). With vol.slot_index the slot is the pool index: the
+// winner only counts the block, a thread that finds its key has its index at
+// once, and nothing is published or waited for. Returns the pool index or -1
+// on error.
 // WAIT = false is the stage-A form used by fallbacks of the tile kernel: a
 // thread that finds its key returns without waiting (returns 0), and the
 // winner publishes without a fence (see warp_insert_nowait).
@@ -335,7 +368,7 @@ template <int P, bool WAIT = true>
 __device__ int insert_block(const VolumeArgs& vol, unsigned long long key, int bx, int by,
                             int bz) {
   unsigned int s = hash_block(bx, by, bz) & vol.mask;
-  for (unsigned int probe = 0; probe < vol.slots; ++probe, s = (s + 1) & vol.mask) {
+  for (unsigned int probe = 0; probe < vol.probe_limit; ++probe, s = (s + 1) & vol.mask) {
     Entry* e = vol.table + s;
     unsigned long long k;
     int idx;
@@ -343,6 +376,10 @@ __device__ int insert_block(const VolumeArgs& vol, unsigned long long key, int b
     if (k == kEmptyKey) {
       const unsigned long long prev = atomicCAS(&e->key, kEmptyKey, key);
       if (prev == kEmptyKey) {
+        if (vol.slot_index) {
+          red_add_u32(&vol.hdr->count, 1u);  // counted only; the slot is the index
+          return static_cast<int>(s);
+        }
         const unsigned int i = atomicAdd(&vol.hdr->count, 1u);
         if (i >= vol.pool) {
           atomicOr(&vol.hdr->err, TSDF_ERRBIT_POOL_FULL);
@@ -361,6 +398,7 @@ __device__ int insert_block(const VolumeArgs& vol, unsigned long long key, int b
       idx = kUnpublished;
     }
     if (k == key) {
+      if (vol.slot_index) return static_cast<int>(s);
       if (!WAIT) return 0;
       return idx >= 0 ? idx : wait_published(vol, e);
     }
@@ -369,7 +407,7 @@ __device__ int insert_block(const VolumeArgs& vol, unsigned long long key, int b
         (load_err_volatile(vol.hdr) & (TSDF_ERRBIT_POOL_FULL | TSDF_ERRBIT_TABLE_FULL)))
       return -1;
   }
-  atomicOr(&vol.hdr->err, TSDF_ERRBIT_TABLE_FULL);
+  probe_exhausted(vol);
   return -1;
 }
 
@@ -414,8 +452,8 @@ __device__ void warp_insert_nowait(const VolumeArgs& vol, unsigned long long key
           todo = false;
         } else {
           s = (s + 1) & vol.mask;
-          if (++probe >= vol.slots) {
-            atomicOr(&vol.hdr->err, TSDF_ERRBIT_TABLE_FULL);
+          if (++probe >= vol.probe_limit) {
+            probe_exhausted(vol);
             todo = false;
           } else if ((probe & 255u) == 0u &&
                      (load_err_volatile(vol.hdr) &
@@ -426,7 +464,10 @@ __device__ void warp_insert_nowait(const VolumeArgs& vol, unsigned long long key
       }
     }
     const unsigned wins = __ballot_sync(0xffffffffu, won);
-    if (wins) {
+    if (wins && vol.slot_index) {
+      // the slot is the index: the block only has to be counted
+      if (static_cast<int>(lane) == __ffs(wins) - 1) red_add_u32(&vol.hdr->count, __popc(wins));
+    } else if (wins) {
       const int leader = __ffs(wins) - 1;
       unsigned base = 0;
       if (static_cast<int>(lane) == leader) base = atomicAdd(&vol.hdr->count, __popc(wins));
@@ -482,14 +523,16 @@ __device__ int warp_insert_get(const VolumeArgs& vol, unsigned long long key, bo
       if (todo) {
         if (k == key) {
           todo = false;
-          if (idx >= 0)
+          if (vol.slot_index)
+            result = static_cast<int>(s);
+          else if (idx >= 0)
             result = idx;
           else if (idx == kUnpublished)
             hit = e;  // wait below, outside the cooperative loop
         } else {
           s = (s + 1) & vol.mask;
-          if (++probe >= vol.slots) {
-            atomicOr(&vol.hdr->err, TSDF_ERRBIT_TABLE_FULL);
+          if (++probe >= vol.probe_limit) {
+            probe_exhausted(vol);
             todo = false;
           } else if ((probe & 255u) == 0u &&
                      (load_err_volatile(vol.hdr) &
@@ -500,7 +543,10 @@ __device__ int warp_insert_get(const VolumeArgs& vol, unsigned long long key, bo
       }
     }
     const unsigned wins = __ballot_sync(0xffffffffu, won);
-    if (wins) {
+    if (wins && vol.slot_index) {
+      if (static_cast<int>(lane) == __ffs(wins) - 1) red_add_u32(&vol.hdr->count, __popc(wins));
+      if (won) result = static_cast<int>(s);
+    } else if (wins) {
       const int leader = __ffs(wins) - 1;
       unsigned base = 0;
       if (static_cast<int>(lane) == leader) base = atomicAdd(&vol.hdr->count, __popc(wins));
@@ -536,9 +582,11 @@ constexpr int kAbsent = -3;  // lookup: key not in the table
 __device__ __forceinline__ int lookup_block(const VolumeArgs& vol, unsigned long long key, int bx,
                                             int by, int bz) {
   unsigned int s = hash_block(bx, by, bz) & vol.mask;
-  for (unsigned int probe = 0; probe < vol.slots; ++probe, s = (s + 1) & vol.mask) {
+  for (unsigned int probe = 0; probe < vol.probe_limit; ++probe, s = (s + 1) & vol.mask) {
     const ulonglong2 ent = __ldg(reinterpret_cast<const ulonglong2*>(vol.table + s));
-    if (ent.x == key) return static_cast<int>(static_cast<unsigned int>(ent.y & 0xFFFFFFFFull));
+    if (ent.x == key)
+      return vol.slot_index ? static_cast<int>(s)
+                            : static_cast<int>(static_cast<unsigned int>(ent.y & 0xFFFFFFFFull));
     if (ent.x == kEmptyKey) return kAbsent;
   }
   return kAbsent;

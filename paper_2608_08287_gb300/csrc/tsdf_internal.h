@@ -39,6 +39,7 @@ struct tsdf_volume {
   tsdf::Offsets off{};
   tsdf::VolumeArgs va{};
   bool poisoned = false;
+  bool dirty = false;          // something was fused since creation or the last reset
   uint32_t* pinned = nullptr;  // {count, err}
   int probe_load = tsdf::kLoadCached;
   int allocate_mode = 1;

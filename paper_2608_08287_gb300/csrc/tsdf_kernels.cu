@@ -420,13 +420,16 @@ __global__ void __launch_bounds__(kThreads)
 // ----------------------------------------------------------------------------
 // read-out and reset
 // ----------------------------------------------------------------------------
+// Means of n blocks (Section 2.2: the pool holds sums). Output block j is pool
+// block list[j], or pool block j when list is null.
 __global__ void export_kernel(const __grid_constant__ VolumeArgs vol, float* __restrict__ out,
-                              unsigned int n) {
+                              unsigned int n, const unsigned int* __restrict__ list) {
   const size_t total = static_cast<size_t>(n) * kBlockVoxels;
-  for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < total;
-       i += static_cast<size_t>(gridDim.x) * blockDim.x) {
-    const size_t blk = i / kBlockVoxels;
-    const size_t l = i % kBlockVoxels;
+  for (size_t j = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; j < total;
+       j += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const size_t blk = j / kBlockVoxels;
+    const size_t l = j % kBlockVoxels;
+    const size_t i = (list ? static_cast<size_t>(list[blk]) : blk) * kBlockVoxels + l;
     const float w = vol.ch[1][i];
     float* o = out + blk * 5 * kBlockVoxels + l;
     const bool any = w > 0.0f;
@@ -437,6 +440,57 @@ __global__ void export_kernel(const __grid_constant__ VolumeArgs vol, float* __r
     o[3 * kBlockVoxels] = any ? __fdiv_rn(vol.ch[3][i], w255) : 0.0f;
     o[4 * kBlockVoxels] = any ? __fdiv_rn(vol.ch[4][i], w255) : 0.0f;
   }
+}
+
+// Slot-index volumes: the occupied slots in slot order, and their block
+// coordinates (from the key), by one CTA of 1024 threads scanning the table
+// 1024 slots at a time with a block-wide prefix sum. Writes at most cap
+// entries; *found receives the number of occupied slots.
+constexpr int kListThreads = 1024;
+__global__ void __launch_bounds__(kListThreads)
+    slot_list_kernel(const __grid_constant__ VolumeArgs vol, unsigned int* __restrict__ list,
+                     int32_t* __restrict__ coords, unsigned int cap,
+                     unsigned int* __restrict__ found) {
+  __shared__ unsigned int warp_count[kListThreads / 32];
+  __shared__ unsigned int warp_excl[kListThreads / 32];
+  __shared__ unsigned int s_total;
+  __shared__ unsigned int base;
+  const unsigned lane = threadIdx.x & 31u, w = threadIdx.x >> 5;
+  if (threadIdx.x == 0) base = 0;
+  for (unsigned int start = 0; start < vol.slots; start += kListThreads) {
+    const unsigned int slot = start + threadIdx.x;
+    const unsigned long long key = slot < vol.slots ? vol.table[slot].key : kEmptyKey;
+    const bool occ = key != kEmptyKey;
+    const unsigned m = __ballot_sync(0xffffffffu, occ);
+    if (lane == 0) warp_count[w] = __popc(m);
+    __syncthreads();
+    if (w == 0) {
+      const unsigned c = warp_count[lane];
+      unsigned incl = c;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= static_cast<unsigned>(o)) incl += t;
+      }
+      warp_excl[lane] = incl - c;
+      if (lane == 31) s_total = incl;
+    }
+    __syncthreads();
+    if (occ) {
+      const unsigned int p = base + warp_excl[w] + __popc(m & ((1u << lane) - 1u));
+      if (p < cap) {
+        int bx, by, bz;
+        unpack_key(key, bx, by, bz);
+        list[p] = slot;
+        coords[3 * static_cast<size_t>(p)] = bx;
+        coords[3 * static_cast<size_t>(p) + 1] = by;
+        coords[3 * static_cast<size_t>(p) + 2] = bz;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) base += s_total;
+  }
+  if (threadIdx.x == 0) *found = base;
 }
 
 // Zero the used prefix [0, min(count, pool)) of every channel; reads the count
@@ -451,6 +505,83 @@ __global__ void clear_used_kernel(const __grid_constant__ VolumeArgs vol) {
 #pragma unroll
     for (int c5 = 0; c5 < 5; ++c5) reinterpret_cast<float4*>(vol.ch[c5])[i] = z;
   }
+}
+
+// Slot-index volumes: zero the pool block of every occupied slot (one warp per
+// slot; the used blocks are scattered over the whole pool). Runs before the
+// table is cleared.
+__global__ void clear_slots_kernel(const __grid_constant__ VolumeArgs vol) {
+  const unsigned lane = threadIdx.x & 31u;
+  const size_t nwarps = (static_cast<size_t>(gridDim.x) * blockDim.x) >> 5;
+  const float4 z = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  for (size_t slot = (blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x) >> 5;
+       slot < vol.slots; slot += nwarps) {
+    if (vol.table[slot].key == kEmptyKey) continue;
+    const size_t q0 = slot * (kBlockVoxels / 4);
+#pragma unroll
+    for (int c5 = 0; c5 < 5; ++c5) {
+      float4* q = reinterpret_cast<float4*>(vol.ch[c5]) + q0;
+#pragma unroll
+      for (int j = 0; j < kBlockVoxels / 4 / 32; ++j) q[lane + 32 * j] = z;
+    }
+  }
+}
+
+// Occupancy and probe lengths of the table, and the total weight in the pool
+// (= contributions received): a diagnostic read-out, not part of fusion.
+__global__ void table_stats_kernel(const __grid_constant__ VolumeArgs vol,
+                                   TableStatsDev* __restrict__ out) {
+  unsigned long long occ = 0, psum = 0;
+  unsigned int pmax = 0;
+  for (size_t slot = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x;
+       slot < vol.slots; slot += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const unsigned long long key = vol.table[slot].key;
+    if (key == kEmptyKey) continue;
+    int bx, by, bz;
+    unpack_key(key, bx, by, bz);
+    const unsigned int home = hash_block(bx, by, bz) & vol.mask;
+    const unsigned int len = ((static_cast<unsigned int>(slot) - home) & vol.mask) + 1u;
+    occ += 1;
+    psum += len;
+    pmax = len > pmax ? len : pmax;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    occ += __shfl_xor_sync(0xffffffffu, occ, o);
+    psum += __shfl_xor_sync(0xffffffffu, psum, o);
+    const unsigned int t = __shfl_xor_sync(0xffffffffu, pmax, o);
+    pmax = t > pmax ? t : pmax;
+  }
+  if ((threadIdx.x & 31u) == 0 && occ) {
+    atomicAdd(&out->occupied, occ);
+    atomicAdd(&out->probe_sum, psum);
+    atomicMax(&out->probe_max, pmax);
+  }
+}
+
+// Sum of all voxel weights of the used blocks (weights are integer counts
+// held exactly in float32; summed as integers). One warp per block.
+__global__ void weight_sum_kernel(const __grid_constant__ VolumeArgs vol,
+                                  TableStatsDev* __restrict__ out) {
+  const unsigned lane = threadIdx.x & 31u;
+  const size_t nwarps = (static_cast<size_t>(gridDim.x) * blockDim.x) >> 5;
+  const unsigned int c = *reinterpret_cast<volatile unsigned int*>(&vol.hdr->count);
+  const size_t nb = vol.slot_index ? vol.slots : (c < vol.pool ? c : vol.pool);
+  unsigned long long sum = 0;
+  for (size_t b = (blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x) >> 5; b < nb;
+       b += nwarps) {
+    if (vol.slot_index && vol.table[b].key == kEmptyKey) continue;
+    const float4* q = reinterpret_cast<const float4*>(vol.ch[1]) + b * (kBlockVoxels / 4);
+#pragma unroll
+    for (int j = 0; j < kBlockVoxels / 4 / 32; ++j) {
+      const float4 w = q[lane + 32 * j];
+      sum += static_cast<unsigned long long>(w.x) + static_cast<unsigned long long>(w.y) +
+             static_cast<unsigned long long>(w.z) + static_cast<unsigned long long>(w.w);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+  if (lane == 0 && sum) atomicAdd(&out->weight_sum, sum);
 }
 
 static inline int tiles_of(int n) { return (n + kTile - 1) / kTile; }
@@ -970,19 +1101,41 @@ cudaError_t launch_batch_status(const BatchHeader* table, unsigned* out, cudaStr
   return cudaGetLastError();
 }
 
-cudaError_t launch_export(const VolumeArgs& vol, float* out, unsigned int n, cudaStream_t s) {
+cudaError_t launch_export(const VolumeArgs& vol, float* out, unsigned int n,
+                          const unsigned int* list, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   const size_t total = static_cast<size_t>(n) * kBlockVoxels;
   const unsigned int grid = static_cast<unsigned int>((total + 255) / 256 < 65535 * 4
                                                           ? (total + 255) / 256
                                                           : 65535 * 4);
-  export_kernel<<<grid, 256, 0, s>>>(vol, out, n);
+  export_kernel<<<grid, 256, 0, s>>>(vol, out, n, list);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_slot_list(const VolumeArgs& vol, unsigned int* list, int32_t* coords,
+                             unsigned int cap, unsigned int* found, cudaStream_t s) {
+  slot_list_kernel<<<1, kListThreads, 0, s>>>(vol, list, coords, cap, found);
   note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_clear_used(const VolumeArgs& vol, int sm_count, cudaStream_t s) {
-  clear_used_kernel<<<sm_count * 8, 256, 0, s>>>(vol);
+  if (vol.slot_index)
+    clear_slots_kernel<<<sm_count * 8, 256, 0, s>>>(vol);
+  else
+    clear_used_kernel<<<sm_count * 8, 256, 0, s>>>(vol);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_table_stats(const VolumeArgs& vol, TableStatsDev* out, int sm_count,
+                               cudaStream_t s) {
+  table_stats_kernel<<<sm_count * 4, 256, 0, s>>>(vol, out);
+  note_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  weight_sum_kernel<<<sm_count * 8, 256, 0, s>>>(vol, out);
   note_launch();
   return cudaGetLastError();
 }

@@ -24,7 +24,19 @@ cudaError_t launch_batch(const BatchHeader* table, int probe_load, int allocate_
                          int integrate_mode, int fuse_mode, int factor, int grid_limit,
                          cudaStream_t s);
 cudaError_t launch_batch_status(const BatchHeader* table, unsigned* out, cudaStream_t s);
-cudaError_t launch_export(const VolumeArgs& vol, float* out, unsigned int n, cudaStream_t s);
+// Means of n blocks into out (n x 5 x 512); block j is pool block list[j], or
+// j when list is null.
+cudaError_t launch_export(const VolumeArgs& vol, float* out, unsigned int n,
+                          const unsigned int* list, cudaStream_t s);
+// Slot-index volumes: occupied slots in slot order (list) and their block
+// coordinates, at most cap of them; *found = occupied slots.
+cudaError_t launch_slot_list(const VolumeArgs& vol, unsigned int* list, int32_t* coords,
+                             unsigned int cap, unsigned int* found, cudaStream_t s);
+// Zero the used pool blocks (before the table is cleared).
 cudaError_t launch_clear_used(const VolumeArgs& vol, int sm_count, cudaStream_t s);
+// Accumulate table occupancy, probe lengths and the pool's total weight into
+// *out (which the caller zeroes first).
+cudaError_t launch_table_stats(const VolumeArgs& vol, TableStatsDev* out, int sm_count,
+                               cudaStream_t s);
 
 }  // namespace tsdf

@@ -21,7 +21,8 @@ from .build import LIB
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OUT_OF_MEMORY", 3: "POOL_FULL", 4: "TABLE_FULL",
           5: "PUBLISH_TIMEOUT", 6: "BOUNDS", 7: "POISONED", 8: "CUDA"}
 OPTIONS = {"probe_load": 0, "publish_timeout_ns": 1, "integrate_mode": 2, "threads": 3,
-           "allocate_mode": 4, "fuse_mode": 5, "ctas_per_sm": 6, "use_graph": 7}
+           "allocate_mode": 4, "fuse_mode": 5, "ctas_per_sm": 6, "use_graph": 7,
+           "slot_index": 8, "probe_bound": 9}
 ERRBITS = {"POOL_FULL": 1, "TABLE_FULL": 2, "PUBLISH_TIMEOUT": 4, "BOUNDS": 8}
 EMPTY_KEY = 0xFFFFFFFFFFFFFFFF
 NOALLOC_MAX_PIXELS = 1 << 20
@@ -38,7 +39,7 @@ EXPORTED = ("tsdf_volume_bytes", "tsdf_volume_create", "tsdf_volume_create_in",
             "tsdf_batch_set_option", "tsdf_fuse_batch_async", "tsdf_batch_status",
             "tsdf_server_create", "tsdf_server_destroy", "tsdf_server_clock",
             "tsdf_server_submit", "tsdf_server_poll", "tsdf_server_pending",
-            "tsdf_server_replay")
+            "tsdf_server_replay", "tsdf_volume_table_stats", "tsdf_volume_copy")
 
 
 class tsdf_intrinsics(ctypes.Structure):
@@ -57,6 +58,12 @@ class tsdf_layout(ctypes.Structure):
                 ("channel", ctypes.c_void_p * 5), ("table_slots", ctypes.c_uint32),
                 ("pool_blocks", ctypes.c_uint32), ("table_offset", ctypes.c_size_t),
                 ("coords_offset", ctypes.c_size_t), ("channel_offset", ctypes.c_size_t * 5)]
+
+
+class tsdf_table_stats(ctypes.Structure):
+    _fields_ = [("occupied_slots", ctypes.c_uint64), ("probe_sum", ctypes.c_uint64),
+                ("probe_max", ctypes.c_uint32), ("blocks", ctypes.c_uint32),
+                ("weight_sum", ctypes.c_uint64)]
 
 
 class tsdf_frame(ctypes.Structure):
@@ -151,6 +158,8 @@ def lib() -> ctypes.CDLL:
             "tsdf_server_pending": (ctypes.c_int, [_P]),
             "tsdf_server_replay": (st, [_P, ctypes.POINTER(tsdf_request), ctypes.c_int,
                                         ctypes.POINTER(tsdf_completion)]),
+            "tsdf_volume_table_stats": (st, [_P, _P, ctypes.POINTER(tsdf_table_stats)]),
+            "tsdf_volume_copy": (st, [_P, _P, _P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -340,6 +349,18 @@ def tsdf_export_blocks(vol, stream=None, voxels=True):
         if st != "OK":
             raise TsdfError(st, "tsdf_export_blocks")
     return coords, vox
+
+
+def tsdf_volume_table_stats(vol, stream=None) -> dict:
+    out = tsdf_table_stats()
+    st = _st(lib().tsdf_volume_table_stats(vol, _stream(stream), ctypes.byref(out)))
+    if st != "OK":
+        raise TsdfError(st, "tsdf_volume_table_stats")
+    return {k: int(getattr(out, k)) for k, _ in tsdf_table_stats._fields_}
+
+
+def tsdf_volume_copy(dst, src, stream=None) -> str:
+    return _st(lib().tsdf_volume_copy(dst, src, _stream(stream)))
 
 
 def tsdf_block_key(bx, by, bz) -> int:
@@ -540,3 +561,9 @@ class Volume:
 
     def layout(self) -> tsdf_layout:
         return tsdf_volume_layout(self.handle)
+
+    def table_stats(self, stream=None) -> dict:
+        return tsdf_volume_table_stats(self.handle, stream)
+
+    def copy_from(self, other, stream=None) -> str:
+        return tsdf_volume_copy(self.handle, other.handle, stream)
