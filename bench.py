@@ -305,6 +305,22 @@ def run_gpu(args, rank, world, local_rank):
             "frac": round(dom[3] / hbm, 4), "algorithmic_bytes": int(dom[1]),
             "traffic": committed_traffic(dom[4])}
 
+    # what the single-frame autotuner picks for this workload (a report: the
+    # headline above times the default configuration)
+    tuning = None
+    if rank == 0 and not args.headline_only:
+        assert vol.reset(sp) == "OK"
+        d, c = dev[0]
+        st, tuning = tsdf.tsdf_autotune_frame(vol.handle, d, W, H, frames[0].intr,
+                                              frames[0].pose, c, 10, sp)
+        tuning = tuning if st == "OK" else {"status": st}
+        # back to the configuration the headline timed
+        for k, x, default in (("allocate_mode", args.allocate_mode, 1),
+                              ("integrate_mode", args.integrate_mode, 0),
+                              ("fuse_mode", args.fuse_mode, 0),
+                              ("probe_load", args.probe_load, 0)):
+            assert vol.set_option(k, default if x is None else x) == "OK"
+
     # end to end through the public C ABI with host buffers
     e2e = run_e2e(args, vol, frames, torch, tsdf, sp, stream, flush, scrub, world)
     vol.close()
@@ -360,6 +376,7 @@ def run_gpu(args, rank, world, local_rank):
                        "blocks_per_frame": mean("blocks"), "voxels_per_frame": mean("voxels")},
             "roofline": roof,
             "e2e": e2e,
+            "autotune_frame": tuning,
             **extra,
             "gpu_launches": int(launches),
             "gpu_launches_detail": "per step: the fusion kernel(s) inside the step events, plus "
@@ -464,13 +481,24 @@ def run_batched(args, torch, tsdf, serving, bank):
     tp = timed(per_frame, args.batch_steps)
     for v in vols:
         assert v.status(sp_) == "OK"
+    # the batch autotuner on the same frames (volumes empty before and after)
+    for v in vols:
+        assert v.reset(sp_) == "OK"
+    st, tuning = batch.autotune(items, reps=5, stream=sp_)
+    assert st == "OK", st
+    timed(batched, 3)
+    tt = timed(batched, args.batch_steps)
+    for v in vols:
+        assert v.status(sp_) == "OK"
         v.close()
     batch.close()
-    mb, mp_ = float(np.mean(tb)), float(np.mean(tp))
+    mb, mp_, mt = float(np.mean(tb)), float(np.mean(tp)), float(np.mean(tt))
     return {"sessions": n, "points_per_step": int(points),
             "batched_pts_per_s": round(points / (mb / 1e3), 1), "batched_ms_per_step": round(mb, 4),
             "per_frame_pts_per_s": round(points / (mp_ / 1e3), 1),
             "per_frame_ms_per_step": round(mp_, 4),
+            "autotuned_pts_per_s": round(points / (mt / 1e3), 1),
+            "autotuned_ms_per_step": round(mt, 4), "autotuned_config": tuning,
             "launches_per_step": {"batched": 2, "per_frame": 2 * n},
             "steps": args.batch_steps, "graph": True}
 

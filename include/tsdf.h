@@ -28,9 +28,13 @@
  * Memory: one device allocation per volume, laid out as
  *   header (block counter, error word) | table (table_slots x 16 B) |
  *   block coordinates (pool_blocks x 3 int32) |
- *   5 channel arrays (pool_blocks x 512 float32 each).
- * A block with pool index i owns floats [i*512, (i+1)*512) of each channel; the
- * voxel (lx, ly, lz) of a block is local index lx + 8*ly + 64*lz.
+ *   voxel sums (pool_blocks x 512 x {tsdf sum, weight, red sum, green sum},
+ *   16 B per voxel) | blue sums (pool_blocks x 512 float32).
+ * The paper keeps the five sums in five parallel float arrays (Section 2.1);
+ * here four of them sit together so that one 16-byte vector reduction adds
+ * them, and the fifth (blue) has an array of its own: 20 bytes per voxel as in
+ * the paper. A block with pool index i owns voxels [i*512, (i+1)*512) of both
+ * arrays; the voxel (lx, ly, lz) of a block is local index lx + 8*ly + 64*lz.
  * Block coordinates are floor(voxel / 8) and must lie in [-2^20, 2^20); the
  * packed key is (bx+2^20)<<42 | (by+2^20)<<21 | (bz+2^20) (Section 2.1).
  *
@@ -86,10 +90,11 @@ typedef struct tsdf_layout {
   uint32_t* error_word;    /* device: sticky error bits, see TSDF_ERRBIT_* */
   void* table;             /* device: table_slots entries {uint64 key; int32 idx; int32 pad} */
   int32_t* block_coords;   /* device: pool_blocks x {bx, by, bz} (unused with TSDF_OPT_SLOT_INDEX) */
-  float* channel[5];       /* device: tsdf sum, weight, red sum, green sum, blue sum */
+  float* voxel_sums;       /* device: pool_blocks x 512 x {tsdf, weight, red, green} sums */
+  float* blue_sums;        /* device: pool_blocks x 512 blue sums */
   uint32_t table_slots;
   uint32_t pool_blocks;
-  size_t table_offset, coords_offset, channel_offset[5]; /* byte offsets from base */
+  size_t table_offset, coords_offset, voxel_sums_offset, blue_sums_offset; /* from base */
 } tsdf_layout;
 
 /* Sticky bits of the device error word. PUBLISH_TIMEOUT is also set when
@@ -318,6 +323,42 @@ tsdf_status tsdf_fuse_batch_async(tsdf_batch* batch, const tsdf_frame* frames, i
  * (per_frame may be NULL; otherwise n >= that batch's size). Returns the first
  * error found, and poisons the volumes that have one. */
 tsdf_status tsdf_batch_status(tsdf_batch* batch, void* stream, tsdf_status* per_frame, int n);
+
+/* ---------------------------------------------------------------------------
+ * Autotuning (not in the paper): time the strategies on the caller's frames
+ * and keep the fastest. Times are medians of `reps` repetitions (1..1000)
+ * after one warm-up, CUDA events on `stream`, L2 evicted before each.
+ * ------------------------------------------------------------------------- */
+
+typedef struct tsdf_tuning {
+  int allocate_mode, integrate_mode, fuse_mode, probe_load; /* the chosen strategy */
+  int ctas_per_sm, use_graph; /* batches: the chosen launch shape (0 for a volume) */
+  int candidates;             /* configurations timed */
+  float best_ms;              /* median time of the chosen configuration */
+  float default_ms;           /* median time of the default configuration */
+} tsdf_tuning;
+
+/* Tune `vol` for this frame: every stage A x stage B strategy, the fused
+ * kernel and the probe loads, each fusing the frame into a scratch copy of the
+ * volume's current state (restored before every repetition). The volume's
+ * contents are not modified; its options are set to the fastest
+ * configuration, which *out describes. Needs device memory for one more
+ * volume of the same size (TSDF_ERR_OUT_OF_MEMORY otherwise). If the frame
+ * overflows the volume the overflow status is returned and nothing is set.
+ * Waits for `stream`. */
+tsdf_status tsdf_autotune_frame(tsdf_volume* vol, const float* depth_dev, int width, int height,
+                                const tsdf_intrinsics* intr, const tsdf_pose* pose,
+                                const uint8_t* rgb_dev, int reps, void* stream,
+                                tsdf_tuning* out);
+
+/* Tune `batch` for these frames: the strategies, then the CTAs-per-SM cap of
+ * the persistent grid (1..4 or all), then graph replay on or off. Every
+ * frame's volume must be empty (nothing fused since creation or reset;
+ * TSDF_ERR_INVALID_ARG otherwise): the volumes are reset before each
+ * repetition and are left empty. The batch's options are set to the fastest
+ * configuration, which *out describes. Waits for `stream`. */
+tsdf_status tsdf_batch_autotune(tsdf_batch* batch, const tsdf_frame* frames, int n, int reps,
+                                void* stream, tsdf_tuning* out);
 
 /* ---------------------------------------------------------------------------
  * Serving: continuous batching of frames from many sessions (not in the

@@ -19,7 +19,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libtsdf.so")
 
 SOURCES = ("tsdf_api.cu", "tsdf_batch.cu", "tsdf_kernels.cu", "tsdf_noalloc.cu",
-           "tsdf_serve.cu")
+           "tsdf_serve.cu", "tsdf_tune.cu")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas",
               "-warn-spills", "--expt-relaxed-constexpr"]

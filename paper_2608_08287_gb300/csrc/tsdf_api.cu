@@ -40,10 +40,10 @@ Offsets offsets_of(uint32_t slots, uint32_t pool) {
   at = align_up(at + static_cast<size_t>(slots) * sizeof(tsdf::Entry));
   o.coords = at;
   at = align_up(at + static_cast<size_t>(pool) * 3 * sizeof(int32_t));
-  for (int c = 0; c < 5; ++c) {
-    o.ch[c] = at;
-    at = align_up(at + static_cast<size_t>(pool) * tsdf::kBlockVoxels * sizeof(float));
-  }
+  o.twrg = at;
+  at = align_up(at + static_cast<size_t>(pool) * tsdf::kBlockVoxels * sizeof(float4));
+  o.blue = at;
+  at = align_up(at + static_cast<size_t>(pool) * tsdf::kBlockVoxels * sizeof(float));
   o.total = at;
   return o;
 }
@@ -76,7 +76,7 @@ tsdf_status enqueue_clear(tsdf_volume* v, cudaStream_t s, bool whole_pool) {
   char* base = static_cast<char*>(v->mem);
   cudaError_t e;
   if (whole_pool) {
-    e = cudaMemsetAsync(base + v->off.ch[0], 0, v->off.total - v->off.ch[0], s);
+    e = cudaMemsetAsync(base + v->off.twrg, 0, v->off.total - v->off.twrg, s);
   } else {
     e = tsdf::launch_clear_used(v->va, v->sm_count, s);
   }
@@ -110,7 +110,8 @@ tsdf_status init_volume(tsdf_volume* v, void* mem, size_t bytes, bool owns, floa
   v->va.slots = slots;
   v->va.coords = reinterpret_cast<int32_t*>(base + v->off.coords);
   v->va.pool = pool;
-  for (int c = 0; c < 5; ++c) v->va.ch[c] = reinterpret_cast<float*>(base + v->off.ch[c]);
+  v->va.twrg = reinterpret_cast<float4*>(base + v->off.twrg);
+  v->va.blue = reinterpret_cast<float*>(base + v->off.blue);
   v->va.timeout_ns = 1000000000ull;
   v->va.probe_limit = slots;
   v->va.slot_index = 0;
@@ -306,10 +307,10 @@ tsdf_status tsdf_volume_layout(const tsdf_volume* vol, tsdf_layout* out) {
   out->error_word = &vol->va.hdr->err;
   out->table = vol->va.table;
   out->block_coords = vol->va.coords;
-  for (int c = 0; c < 5; ++c) {
-    out->channel[c] = vol->va.ch[c];
-    out->channel_offset[c] = vol->off.ch[c];
-  }
+  out->voxel_sums = reinterpret_cast<float*>(vol->va.twrg);
+  out->blue_sums = vol->va.blue;
+  out->voxel_sums_offset = vol->off.twrg;
+  out->blue_sums_offset = vol->off.blue;
   out->table_slots = vol->slots;
   out->pool_blocks = vol->pool;
   out->table_offset = vol->off.table;

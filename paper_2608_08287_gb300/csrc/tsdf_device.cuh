@@ -83,7 +83,11 @@ struct VolumeArgs {
   unsigned int slots;
   int32_t* coords;         // pool x 3
   unsigned int pool;
-  float* ch[5];            // tsdf sum, weight, r sum, g sum, b sum
+  // The five sums of a voxel (Section 2.1), split 4 + 1 so that one vector
+  // reduction carries four of them: pool x 512 records {tsdf sum, weight,
+  // red sum, green sum} and pool x 512 blue sums.
+  float4* twrg;
+  float* blue;
   Header* hdr;
   unsigned long long timeout_ns;
   // Probes before a scan gives up: table_slots (unbounded in the paper's
@@ -270,6 +274,30 @@ __device__ __forceinline__ unsigned walk_point(const FrameArgs& f, const Ray& r,
 // kernel holds other atomics.
 __device__ __forceinline__ void red_add(float* p, float v) {
   asm volatile("red.relaxed.gpu.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+}
+
+__device__ __forceinline__ void red_add_v4(float4* p, float a, float b, float c, float d) {
+  asm volatile("red.relaxed.gpu.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a),
+               "f"(b), "f"(c), "f"(d)
+               : "memory");
+}
+
+__device__ __forceinline__ void red_add_v2(float4* p, float a, float b) {
+  asm volatile("red.relaxed.gpu.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(a), "f"(b)
+               : "memory");
+}
+
+// One contribution to voxel o of the pool (Section 2.2, "Update"): tsdf and a
+// weight of 1, and the point's colour when the frame has one -- five sums in
+// two fire-and-forget reductions (one 16-byte vector, one scalar).
+__device__ __forceinline__ void add_contribution(float4* twrg, float* blue, size_t o, float t,
+                                                 bool colour, float cr, float cg, float cb) {
+  if (colour) {
+    red_add_v4(twrg + o, t, 1.0f, cr, cg);
+    red_add(blue + o, cb);
+  } else {
+    red_add_v2(twrg + o, t, 1.0f);
+  }
 }
 
 // Stored value: truncated, normalised signed distance at the voxel centre.

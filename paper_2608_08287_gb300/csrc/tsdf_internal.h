@@ -17,7 +17,7 @@ inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 // Byte offsets of a volume's sections inside its one allocation.
 struct Offsets {
-  size_t table, coords, ch[5], total;
+  size_t table, coords, twrg, blue, total;
 };
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }

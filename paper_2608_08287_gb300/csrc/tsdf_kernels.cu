@@ -297,14 +297,8 @@ __device__ __forceinline__ void tile_collect(TileShared& T, const FrameArgs& f,
 __device__ __forceinline__ void add_voxel_direct(const VolumeArgs& vol, int idx, int l, float t,
                                                  bool colour, float cr, float cg, float cb) {
   if (idx < 0) return;
-  const size_t o = static_cast<size_t>(idx) * kBlockVoxels + l;
-  red_add(vol.ch[0] + o, t);
-  red_add(vol.ch[1] + o, 1.0f);
-  if (colour) {
-    red_add(vol.ch[2] + o, cr);
-    red_add(vol.ch[3] + o, cg);
-    red_add(vol.ch[4] + o, cb);
-  }
+  add_contribution(vol.twrg, vol.blue, static_cast<size_t>(idx) * kBlockVoxels + l, t, colour,
+                   cr, cg, cb);
 }
 
 // Stage A, tile strategy, for one 16x16 pixel tile: the tile's distinct keys
@@ -360,14 +354,9 @@ __device__ __forceinline__ void scatter_add(const FrameArgs& f, const VolumeArgs
     bc.idx = resolve_for_update(vol, lookup_block(vol, key, bx, by, bz));
   }
   if (bc.idx < 0) return;
-  const size_t o = static_cast<size_t>(bc.idx) * kBlockVoxels + local_index(gx, gy, gz);
-  red_add(vol.ch[0] + o, tsdf_value(f, r.d, zc));
-  red_add(vol.ch[1] + o, 1.0f);
-  if (colour) {
-    red_add(vol.ch[2] + o, cr);
-    red_add(vol.ch[3] + o, cg);
-    red_add(vol.ch[4] + o, cb);
-  }
+  add_contribution(vol.twrg, vol.blue,
+                   static_cast<size_t>(bc.idx) * kBlockVoxels + local_index(gx, gy, gz),
+                   tsdf_value(f, r.d, zc), colour, cr, cg, cb);
 }
 
 // Stage B, the paper's update, for the 256 points of one tile (each thread
@@ -430,15 +419,16 @@ __global__ void export_kernel(const __grid_constant__ VolumeArgs vol, float* __r
     const size_t blk = j / kBlockVoxels;
     const size_t l = j % kBlockVoxels;
     const size_t i = (list ? static_cast<size_t>(list[blk]) : blk) * kBlockVoxels + l;
-    const float w = vol.ch[1][i];
+    const float4 s = vol.twrg[i];
+    const float w = s.y;
     float* o = out + blk * 5 * kBlockVoxels + l;
     const bool any = w > 0.0f;
     const float w255 = w * 255.0f;  // exact while w < 65793
-    o[0] = any ? __fdiv_rn(vol.ch[0][i], w) : 0.0f;
+    o[0] = any ? __fdiv_rn(s.x, w) : 0.0f;
     o[kBlockVoxels] = w;
-    o[2 * kBlockVoxels] = any ? __fdiv_rn(vol.ch[2][i], w255) : 0.0f;
-    o[3 * kBlockVoxels] = any ? __fdiv_rn(vol.ch[3][i], w255) : 0.0f;
-    o[4 * kBlockVoxels] = any ? __fdiv_rn(vol.ch[4][i], w255) : 0.0f;
+    o[2 * kBlockVoxels] = any ? __fdiv_rn(s.z, w255) : 0.0f;
+    o[3 * kBlockVoxels] = any ? __fdiv_rn(s.w, w255) : 0.0f;
+    o[4 * kBlockVoxels] = any ? __fdiv_rn(vol.blue[i], w255) : 0.0f;
   }
 }
 
@@ -493,8 +483,8 @@ __global__ void __launch_bounds__(kListThreads)
   if (threadIdx.x == 0) *found = base;
 }
 
-// Zero the used prefix [0, min(count, pool)) of every channel; reads the count
-// on the device so the host needs no round trip.
+// Zero the used prefix [0, min(count, pool)) of the pool's sums; reads the
+// count on the device so the host needs no round trip.
 __global__ void clear_used_kernel(const __grid_constant__ VolumeArgs vol) {
   const unsigned int c = *reinterpret_cast<volatile unsigned int*>(&vol.hdr->count);
   const unsigned int n = c < vol.pool ? c : vol.pool;
@@ -503,7 +493,8 @@ __global__ void clear_used_kernel(const __grid_constant__ VolumeArgs vol) {
   for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < quads;
        i += static_cast<size_t>(gridDim.x) * blockDim.x) {
 #pragma unroll
-    for (int c5 = 0; c5 < 5; ++c5) reinterpret_cast<float4*>(vol.ch[c5])[i] = z;
+    for (int j = 0; j < 4; ++j) vol.twrg[4 * i + j] = z;
+    reinterpret_cast<float4*>(vol.blue)[i] = z;
   }
 }
 
@@ -517,13 +508,12 @@ __global__ void clear_slots_kernel(const __grid_constant__ VolumeArgs vol) {
   for (size_t slot = (blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x) >> 5;
        slot < vol.slots; slot += nwarps) {
     if (vol.table[slot].key == kEmptyKey) continue;
-    const size_t q0 = slot * (kBlockVoxels / 4);
+    float4* t = vol.twrg + slot * kBlockVoxels;
 #pragma unroll
-    for (int c5 = 0; c5 < 5; ++c5) {
-      float4* q = reinterpret_cast<float4*>(vol.ch[c5]) + q0;
+    for (int j = 0; j < kBlockVoxels / 32; ++j) t[lane + 32 * j] = z;
+    float4* q = reinterpret_cast<float4*>(vol.blue) + slot * (kBlockVoxels / 4);
 #pragma unroll
-      for (int j = 0; j < kBlockVoxels / 4 / 32; ++j) q[lane + 32 * j] = z;
-    }
+    for (int j = 0; j < kBlockVoxels / 4 / 32; ++j) q[lane + 32 * j] = z;
   }
 }
 
@@ -571,13 +561,10 @@ __global__ void weight_sum_kernel(const __grid_constant__ VolumeArgs vol,
   for (size_t b = (blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x) >> 5; b < nb;
        b += nwarps) {
     if (vol.slot_index && vol.table[b].key == kEmptyKey) continue;
-    const float4* q = reinterpret_cast<const float4*>(vol.ch[1]) + b * (kBlockVoxels / 4);
+    const float4* q = vol.twrg + b * kBlockVoxels;
 #pragma unroll
-    for (int j = 0; j < kBlockVoxels / 4 / 32; ++j) {
-      const float4 w = q[lane + 32 * j];
-      sum += static_cast<unsigned long long>(w.x) + static_cast<unsigned long long>(w.y) +
-             static_cast<unsigned long long>(w.z) + static_cast<unsigned long long>(w.w);
-    }
+    for (int j = 0; j < kBlockVoxels / 32; ++j)
+      sum += static_cast<unsigned long long>(q[lane + 32 * j].y);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);

@@ -39,7 +39,8 @@ EXPORTED = ("tsdf_volume_bytes", "tsdf_volume_create", "tsdf_volume_create_in",
             "tsdf_batch_set_option", "tsdf_fuse_batch_async", "tsdf_batch_status",
             "tsdf_server_create", "tsdf_server_destroy", "tsdf_server_clock",
             "tsdf_server_submit", "tsdf_server_poll", "tsdf_server_pending",
-            "tsdf_server_replay", "tsdf_volume_table_stats", "tsdf_volume_copy")
+            "tsdf_server_replay", "tsdf_volume_table_stats", "tsdf_volume_copy",
+            "tsdf_autotune_frame", "tsdf_batch_autotune")
 
 
 class tsdf_intrinsics(ctypes.Structure):
@@ -55,15 +56,24 @@ class tsdf_layout(ctypes.Structure):
     _fields_ = [("base", ctypes.c_void_p), ("bytes", ctypes.c_size_t),
                 ("block_count", ctypes.c_void_p), ("error_word", ctypes.c_void_p),
                 ("table", ctypes.c_void_p), ("block_coords", ctypes.c_void_p),
-                ("channel", ctypes.c_void_p * 5), ("table_slots", ctypes.c_uint32),
-                ("pool_blocks", ctypes.c_uint32), ("table_offset", ctypes.c_size_t),
-                ("coords_offset", ctypes.c_size_t), ("channel_offset", ctypes.c_size_t * 5)]
+                ("voxel_sums", ctypes.c_void_p), ("blue_sums", ctypes.c_void_p),
+                ("table_slots", ctypes.c_uint32), ("pool_blocks", ctypes.c_uint32),
+                ("table_offset", ctypes.c_size_t), ("coords_offset", ctypes.c_size_t),
+                ("voxel_sums_offset", ctypes.c_size_t), ("blue_sums_offset", ctypes.c_size_t)]
 
 
 class tsdf_table_stats(ctypes.Structure):
     _fields_ = [("occupied_slots", ctypes.c_uint64), ("probe_sum", ctypes.c_uint64),
                 ("probe_max", ctypes.c_uint32), ("blocks", ctypes.c_uint32),
                 ("weight_sum", ctypes.c_uint64)]
+
+
+class tsdf_tuning(ctypes.Structure):
+    _fields_ = [("allocate_mode", ctypes.c_int), ("integrate_mode", ctypes.c_int),
+                ("fuse_mode", ctypes.c_int), ("probe_load", ctypes.c_int),
+                ("ctas_per_sm", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("candidates", ctypes.c_int), ("best_ms", ctypes.c_float),
+                ("default_ms", ctypes.c_float)]
 
 
 class tsdf_frame(ctypes.Structure):
@@ -160,6 +170,12 @@ def lib() -> ctypes.CDLL:
                                         ctypes.POINTER(tsdf_completion)]),
             "tsdf_volume_table_stats": (st, [_P, _P, ctypes.POINTER(tsdf_table_stats)]),
             "tsdf_volume_copy": (st, [_P, _P, _P]),
+            "tsdf_autotune_frame": (st, [_P, _P, ctypes.c_int, ctypes.c_int,
+                                         ctypes.POINTER(tsdf_intrinsics),
+                                         ctypes.POINTER(tsdf_pose), _P, ctypes.c_int, _P,
+                                         ctypes.POINTER(tsdf_tuning)]),
+            "tsdf_batch_autotune": (st, [_P, ctypes.POINTER(tsdf_frame), ctypes.c_int,
+                                         ctypes.c_int, _P, ctypes.POINTER(tsdf_tuning)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -363,6 +379,30 @@ def tsdf_volume_copy(dst, src, stream=None) -> str:
     return _st(lib().tsdf_volume_copy(dst, src, _stream(stream)))
 
 
+def _tuning(t):
+    return {k: (float(getattr(t, k)) if k.endswith("_ms") else int(getattr(t, k)))
+            for k, _ in tsdf_tuning._fields_}
+
+
+def tsdf_autotune_frame(vol, depth, width, height, intr, pose, rgb=None, reps=5,
+                        stream=None):
+    """(status, tuning dict or None)."""
+    out = tsdf_tuning()
+    st = _st(lib().tsdf_autotune_frame(vol, _dptr(depth), int(width), int(height), _intr(intr),
+                                       _pose(pose), _dptr(rgb), int(reps), _stream(stream),
+                                       ctypes.byref(out)))
+    return st, (_tuning(out) if st == "OK" else None)
+
+
+def tsdf_batch_autotune(batch, frames, n=None, reps=5, stream=None):
+    """(status, tuning dict or None) for a ctypes array of tsdf_frame."""
+    n = len(frames) if n is None else n
+    out = tsdf_tuning()
+    st = _st(lib().tsdf_batch_autotune(batch, frames, int(n), int(reps), _stream(stream),
+                                       ctypes.byref(out)))
+    return st, (_tuning(out) if st == "OK" else None)
+
+
 def tsdf_block_key(bx, by, bz) -> int:
     return int(lib().tsdf_block_key(bx, by, bz))
 
@@ -503,6 +543,12 @@ class Batch:
     def status(self, n, stream=None):
         return tsdf_batch_status(self.handle, n, stream)
 
+    def autotune(self, items, reps=5, stream=None):
+        """items as for fuse_async; their volumes must be empty and are left empty."""
+        frames = make_frames([(v.handle, d, c, i, p) for v, d, c, i, p in items])
+        self._keep = (frames, items)
+        return tsdf_batch_autotune(self.handle, frames, len(items), reps, stream)
+
 
 # ----------------------------------------------------------------------------
 # convenience: an owning handle
@@ -561,6 +607,10 @@ class Volume:
 
     def layout(self) -> tsdf_layout:
         return tsdf_volume_layout(self.handle)
+
+    def autotune(self, depth, intr, pose, rgb=None, reps=5, stream=None):
+        h, w = depth.shape[-2], depth.shape[-1]
+        return tsdf_autotune_frame(self.handle, depth, w, h, intr, pose, rgb, reps, stream)
 
     def table_stats(self, stream=None) -> dict:
         return tsdf_volume_table_stats(self.handle, stream)

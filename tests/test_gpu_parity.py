@@ -324,6 +324,36 @@ def test_publish_timeout_is_bounded(mode):
     assert_same_volume(gv, ov)
 
 
+def test_layout_sums_match_export():
+    """The pool layout the header documents: per voxel a 16-byte record {tsdf
+    sum, weight, red sum, green sum}, and a separate array of blue sums; the
+    export's means are those sums divided by the weight."""
+    f = synth.room_frame(4, width=320, height=240)
+    spec = synth.VolumeSpec(0.005, 0.02, 1 << 16, 1 << 15)
+    nbytes = tsdf.tsdf_volume_bytes(spec.table_slots, spec.pool_blocks)
+    assert nbytes >= spec.pool_blocks * 512 * 20
+    mem = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    gv = tsdf.Volume(spec.voxel_size, spec.truncation, spec.table_slots, spec.pool_blocks,
+                     memory=mem)
+    d, c = to_dev(f)
+    assert gv.fuse(d, f.intr, f.pose, c) == "OK"
+    coords, vox = gv.export()          # pool order: block j is pool index j
+    n = len(coords)
+    lay = gv.layout()
+    sums = mem[lay.voxel_sums_offset:lay.voxel_sums_offset + 16 * 512 * n].cpu().numpy()
+    sums = sums.view(np.float32).reshape(n, 512, 4)
+    blue = mem[lay.blue_sums_offset:lay.blue_sums_offset + 4 * 512 * n].cpu().numpy()
+    blue = blue.view(np.float32).reshape(n, 512)
+    w = sums[:, :, 1]
+    assert np.array_equal(w, vox[:, 1])
+    hit = w > 0
+    assert np.array_equal(sums[:, :, 0][hit] / w[hit], vox[:, 0][hit])
+    assert np.array_equal(sums[:, :, 2][hit] / (w[hit] * 255), vox[:, 2][hit])
+    assert np.array_equal(sums[:, :, 3][hit] / (w[hit] * 255), vox[:, 3][hit])
+    assert np.array_equal(blue[hit] / (w[hit] * 255), vox[:, 4][hit])
+    assert not np.any(sums[~hit]) and not np.any(blue[~hit])
+
+
 def test_block_coordinates_match_table():
     """Every published index points at a coordinate row that matches its key."""
     f = synth.room_frame(2, width=320, height=240)
