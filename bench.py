@@ -321,6 +321,12 @@ def run_gpu(args, rank, world, local_rank):
                               ("probe_load", args.probe_load, 0)):
             assert vol.set_option(k, default if x is None else x) == "OK"
 
+    # surface extraction of the four frames fused together (compute timed
+    # apart from the device-to-host copy, as the paper splits it)
+    extraction = None
+    if rank == 0 and not args.headline_only:
+        extraction = run_extraction(args, vol, frames, dev, tsdf, sp, hbm)
+
     # end to end through the public C ABI with host buffers
     e2e = run_e2e(args, vol, frames, torch, tsdf, sp, stream, flush, scrub, world)
     vol.close()
@@ -377,6 +383,7 @@ def run_gpu(args, rank, world, local_rank):
             "roofline": roof,
             "e2e": e2e,
             "autotune_frame": tuning,
+            "extraction": extraction,
             **extra,
             "gpu_launches": int(launches),
             "gpu_launches_detail": "per step: the fusion kernel(s) inside the step events, plus "
@@ -388,6 +395,31 @@ def run_gpu(args, rank, world, local_rank):
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     return out
+
+
+def run_extraction(args, vol, frames, dev, tsdf, sp, hbm):
+    """Marching tetrahedra over the bench frames fused into one volume:
+    kernel time and device-to-host copy time of the triangle soup, medians
+    of 10 calls through tsdf_extract_mesh."""
+    W, H = 640, 480
+    assert vol.reset(sp) == "OK"
+    for f, (d, c) in zip(frames, dev):
+        assert tsdf.tsdf_fuse_frame(vol.handle, d, W, H, f.intr, f.pose, c, sp) == "OK"
+    blocks = vol.block_count(sp)
+    runs = [vol.extract_mesh(sp, cells=False) for _ in range(11)][1:]
+    n = len(runs[0][0])
+    comp = float(np.median([r[2]["compute_ms"] for r in runs]))
+    d2h = float(np.median([r[2]["d2h_ms"] for r in runs]))
+    nbytes = runs[0][2]["d2h_bytes"]
+    # algorithmic bytes: the {tsdf, weight} sums of every allocated voxel read
+    # once (16-byte records), the triangles written once
+    alg = blocks * 512 * 16 + n * 36
+    return {"frames_fused": len(frames), "blocks": blocks, "triangles": n,
+            "compute_ms": round(comp, 4), "d2h_ms": round(d2h, 4),
+            "d2h_bytes": nbytes, "d2h_gbs": round(nbytes / (d2h * 1e6), 1) if d2h else None,
+            "kernel_algorithmic_bytes": alg,
+            "kernel_hbm_frac": round(alg / (comp * 1e6) / hbm, 4),
+            "call": "tsdf_extract_mesh (triangles only, pageable host buffer)"}
 
 
 def run_e2e(args, vol, frames, torch, tsdf, sp, stream, flush, scrub, world=1):

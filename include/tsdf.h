@@ -433,6 +433,48 @@ tsdf_status tsdf_server_replay(tsdf_server* server, const tsdf_request* requests
 tsdf_status tsdf_export_blocks(tsdf_volume* vol, int32_t* coords_host, float* voxels_host,
                                uint32_t capacity, uint32_t* n_out, void* stream);
 
+/* Surface extraction: marching tetrahedra over the allocated blocks (the
+ * extraction stage of Section 2, which the paper runs once in CUDA C++ and
+ * excludes from its comparison; Section 2 also reports that most of its
+ * measured time was the device-to-host copy, so the two are timed apart).
+ *   - grid points are voxel centres (g + 1/2) * voxel_size; every voxel g
+ *     whose 8 corners g + {0,1}^3 all have weight > 0 spans a cube; a corner's
+ *     value is its mean tsdf;
+ *   - each cube is split into the 6 tetrahedra around its diagonal from corner
+ *     0 to corner 7 (corner c = g + (c&1, c>>1&1, c>>2&1));
+ *   - a corner is inside when its value is < 0; each tetrahedron edge with
+ *     ends on both sides holds a vertex p_lo + t (p_hi - p_lo),
+ *     t = v_lo / (v_lo - v_hi), lo the corner whose offset bits are a subset
+ *     of the other's;
+ *   - one lone corner gives one triangle, a pair gives two; every triangle is
+ *     wound so its normal points towards positive values (free space).
+ * A triangle is 9 float32 (x, y, z of three vertices, metres); its cell record
+ * is 4 int32 {gx, gy, gz, 2*tetrahedron + k}: the cube's voxel and which
+ * triangle of which tetrahedron it is. Triangle order is unspecified. */
+
+typedef struct tsdf_extract_timing {
+  float compute_ms;   /* the extraction kernel (CUDA events) */
+  float d2h_ms;       /* the device-to-host copies of the result */
+  uint64_t d2h_bytes; /* bytes copied to the host */
+} tsdf_extract_timing;
+
+/* Enqueue the extraction into device buffers: at most `capacity` triangles
+ * and cell records are written (either pointer may be NULL), and *count_dev
+ * (device) receives the total number of triangles, which may exceed
+ * capacity. Nothing is allocated; nothing waits. */
+tsdf_status tsdf_extract_mesh_async(tsdf_volume* vol, float* triangles_dev, int32_t* cells_dev,
+                                    uint32_t capacity, uint32_t* count_dev, void* stream);
+
+/* Extract to host memory: triangles_host gets n x 9 floats, cells_host
+ * n x 4 int32 (either may be NULL; both NULL or capacity 0 only counts).
+ * *n_out is always n. If capacity < n nothing is copied and
+ * TSDF_ERR_INVALID_ARG is returned. *timing (nullable) receives the kernel
+ * and copy times. Allocates device scratch for the result; waits for
+ * `stream`. */
+tsdf_status tsdf_extract_mesh(tsdf_volume* vol, float* triangles_host, int32_t* cells_host,
+                              uint32_t capacity, uint32_t* n_out, tsdf_extract_timing* timing,
+                              void* stream);
+
 /* Diagnostics of a volume's table and pool (a read-out, not part of fusion).
  * A key's probe length is its distance from its home slot plus one: the
  * number of entries an unbounded probe reads to find it (Section 3.1, linear

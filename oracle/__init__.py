@@ -65,6 +65,12 @@ def lib():
             L.oracle_export_some.restype = None
             L.oracle_export_some.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32,
                                              ctypes.c_void_p, ctypes.c_void_p]
+            L.oracle_extract.restype = ctypes.c_uint32
+            L.oracle_extract.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_uint32]
+            L.oracle_set_voxel.restype = ctypes.c_int
+            L.oracle_set_voxel.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                           ctypes.c_int32, ctypes.c_double, ctypes.c_uint32]
             L.oracle_export.restype = ctypes.c_uint32
             L.oracle_export.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_uint32]
@@ -138,6 +144,22 @@ class OracleVolume:
         if n:
             self._L.oracle_export(self._h, _ptr(coords), None, None, n)
         return coords
+
+    def extract(self):
+        """Marching tetrahedra (readings E1-E4 in tsdf_oracle.cpp):
+        (triangles (n,3,3) float64, cells (n,4) int32 {gx, gy, gz, 2*tet+sub})."""
+        n = int(self._L.oracle_extract(self._h, None, None, 0))
+        tris = np.zeros((n, 3, 3), dtype=np.float64)
+        cells = np.zeros((n, 4), dtype=np.int32)
+        if n:
+            self._L.oracle_extract(self._h, _ptr(tris), _ptr(cells), n)
+        return tris, cells
+
+    def set_voxel(self, gx, gy, gz, tsdf_sum, weight=1):
+        """Write one voxel's tsdf sum and weight directly (hand-built grids)."""
+        if self._L.oracle_set_voxel(self._h, int(gx), int(gy), int(gz), float(tsdf_sum),
+                                    int(weight)):
+            raise ValueError("pool exhausted")
 
     def export_some(self, coords):
         """(found (n,) bool, voxels (n,5,512) float64) for the given block coordinates."""

@@ -474,6 +474,81 @@ tsdf_status tsdf_export_blocks(tsdf_volume* vol, int32_t* coords_host, float* vo
   return from_cuda(e);
 }
 
+tsdf_status tsdf_extract_mesh_async(tsdf_volume* vol, float* triangles_dev, int32_t* cells_dev,
+                                    uint32_t capacity, uint32_t* count_dev, void* stream) {
+  if (!vol || !count_dev) return TSDF_ERR_INVALID_ARG;
+  if (capacity && !triangles_dev && !cells_dev) return TSDF_ERR_INVALID_ARG;
+  cudaStream_t s = as_stream(stream);
+  cudaError_t e = cudaMemsetAsync(count_dev, 0, sizeof(uint32_t), s);
+  if (e == cudaSuccess)
+    e = tsdf::launch_extract(vol->va, vol->voxel, triangles_dev, cells_dev, capacity, count_dev,
+                             vol->sm_count, s);
+  return from_cuda(e);
+}
+
+tsdf_status tsdf_extract_mesh(tsdf_volume* vol, float* triangles_host, int32_t* cells_host,
+                              uint32_t capacity, uint32_t* n_out, tsdf_extract_timing* timing,
+                              void* stream) {
+  if (!vol || !n_out) return TSDF_ERR_INVALID_ARG;
+  cudaStream_t s = as_stream(stream);
+  const bool fetch = (triangles_host || cells_host) && capacity > 0;
+  const size_t tri_bytes = triangles_host ? static_cast<size_t>(capacity) * 9 * sizeof(float) : 0;
+  const size_t cell_bytes = cells_host ? static_cast<size_t>(capacity) * 4 * sizeof(int32_t) : 0;
+  char* buf = nullptr;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreate(&ev[i]);
+  if (e == cudaSuccess)
+    e = cudaMallocAsync(reinterpret_cast<void**>(&buf),
+                        kAlign + (fetch ? align_up(tri_bytes) + cell_bytes : 0), s);
+  uint32_t* counter = reinterpret_cast<uint32_t*>(buf);
+  float* tris = fetch && triangles_host ? reinterpret_cast<float*>(buf + kAlign) : nullptr;
+  int32_t* cells =
+      fetch && cells_host ? reinterpret_cast<int32_t*>(buf + kAlign + align_up(tri_bytes)) : nullptr;
+  if (e == cudaSuccess) e = cudaEventRecord(ev[0], s);
+  tsdf_status st = from_cuda(e);
+  if (st == TSDF_OK)
+    st = tsdf_extract_mesh_async(vol, tris, cells, fetch ? capacity : 0, counter, stream);
+  if (st == TSDF_OK) st = from_cuda(cudaEventRecord(ev[1], s));
+  if (st == TSDF_OK)
+    st = from_cuda(cudaMemcpyAsync(vol->pinned, counter, sizeof(uint32_t),
+                                   cudaMemcpyDeviceToHost, s));
+  if (st == TSDF_OK) st = from_cuda(cudaStreamSynchronize(s));
+  uint32_t n = 0;
+  if (st == TSDF_OK) {
+    n = vol->pinned[0];
+    *n_out = n;
+    if (fetch && n > capacity) st = TSDF_ERR_INVALID_ARG;  // nothing is copied
+  }
+  float d2h_ms = 0.0f, compute_ms = 0.0f;
+  if (st == TSDF_OK && fetch && n > 0) {
+    e = cudaEventRecord(ev[2], s);
+    if (e == cudaSuccess && triangles_host)
+      e = cudaMemcpyAsync(triangles_host, tris, static_cast<size_t>(n) * 9 * sizeof(float),
+                          cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && cells_host)
+      e = cudaMemcpyAsync(cells_host, cells, static_cast<size_t>(n) * 4 * sizeof(int32_t),
+                          cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[3], s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&d2h_ms, ev[2], ev[3]);
+    st = from_cuda(e);
+  }
+  if (st == TSDF_OK) st = from_cuda(cudaEventElapsedTime(&compute_ms, ev[0], ev[1]));
+  if (buf) cudaFreeAsync(buf, s);
+  cudaStreamSynchronize(s);
+  for (int i = 0; i < 4; ++i)
+    if (ev[i]) cudaEventDestroy(ev[i]);
+  if (st == TSDF_OK && timing) {
+    timing->compute_ms = compute_ms;
+    timing->d2h_ms = d2h_ms;
+    timing->d2h_bytes = fetch ? static_cast<uint64_t>(n) *
+                                    ((triangles_host ? 36u : 0u) + (cells_host ? 16u : 0u))
+                              : 0;
+  }
+  return st;
+}
+
 tsdf_status tsdf_volume_table_stats(tsdf_volume* vol, void* stream, tsdf_table_stats* out) {
   if (!vol || !out) return TSDF_ERR_INVALID_ARG;
   cudaStream_t s = as_stream(stream);

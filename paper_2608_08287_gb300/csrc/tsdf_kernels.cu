@@ -571,6 +571,201 @@ __global__ void weight_sum_kernel(const __grid_constant__ VolumeArgs vol,
   if (lane == 0 && sum) atomicAdd(&out->weight_sum, sum);
 }
 
+// ----------------------------------------------------------------------------
+// surface extraction: marching tetrahedra over the allocated blocks
+// ----------------------------------------------------------------------------
+// The grid points are voxel centres; every voxel whose 8 corners g + {0,1}^3
+// are all observed (weight > 0) spans a cube, split into the 6 tetrahedra
+// around its 0-7 diagonal; a corner is inside when its mean tsdf is < 0; each
+// tetrahedron edge with ends on both sides holds a vertex at the linear zero
+// crossing, measured from its lower corner; triangles are wound with normals
+// towards positive values. One CTA of 512 threads per block: the block's
+// means and the faces of its 7 upper neighbours (looked up in the table) are
+// staged as a 9x9x9 tile in shared memory, NaN where unobserved; each thread
+// takes one cube, counts its triangles, the warp reserves space with one
+// atomicAdd, and the thread writes them.
+constexpr int kExtractThreads = 512;
+
+// Tetrahedra of a cube, positively oriented; corner c = g + (c&1, c>>1&1, c>>2&1).
+__constant__ unsigned char c_tets[6][4] = {{0, 1, 3, 7}, {0, 1, 7, 5}, {0, 2, 7, 3},
+                                           {0, 2, 6, 7}, {0, 4, 5, 7}, {0, 4, 7, 6}};
+// For a lone corner at position i: an even reordering of the four that puts it first.
+__constant__ unsigned char c_lone[4][4] = {{0, 1, 2, 3}, {1, 0, 3, 2}, {2, 0, 1, 3}, {3, 0, 2, 1}};
+// For an inside pair, indexed by its 4-bit mask: an even reordering that puts
+// the pair first (unused masks hold zeros).
+__constant__ unsigned char c_pair[16][4] = {
+    {0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}, {0, 1, 2, 3}, {0, 0, 0, 0}, {0, 2, 3, 1},
+    {1, 2, 0, 3}, {0, 0, 0, 0}, {0, 0, 0, 0}, {0, 3, 1, 2}, {1, 3, 2, 0}, {0, 0, 0, 0},
+    {2, 3, 0, 1}, {0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}};
+
+struct CubeCorners {
+  float val[8];
+  int gx, gy, gz;
+  float v;
+};
+
+// Vertex on the edge between cube corners a and b (either order).
+__device__ __forceinline__ void edge_vertex(const CubeCorners& C, int a, int b, float* out) {
+  const int lo = ((a & b) == a) ? a : b;
+  const int hi = lo ^ a ^ b;
+  const float t = __fdiv_rn(C.val[lo], __fsub_rn(C.val[lo], C.val[hi]));
+  const int g[3] = {C.gx, C.gy, C.gz};
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float plo = __fmul_rn(__fadd_rn(static_cast<float>(g[k] + ((lo >> k) & 1)), 0.5f), C.v);
+    const float phi = __fmul_rn(__fadd_rn(static_cast<float>(g[k] + ((hi >> k) & 1)), 0.5f), C.v);
+    out[k] = __fadd_rn(plo, __fmul_rn(t, __fsub_rn(phi, plo)));
+  }
+}
+
+__device__ __forceinline__ void write_triangle(const CubeCorners& C, int e0a, int e0b, int e1a,
+                                               int e1b, int e2a, int e2b, int tag,
+                                               unsigned pos, unsigned capacity, float* tris,
+                                               int32_t* cells) {
+  if (pos >= capacity) return;
+  if (tris) {
+    float* o = tris + 9 * static_cast<size_t>(pos);
+    edge_vertex(C, e0a, e0b, o);
+    edge_vertex(C, e1a, e1b, o + 3);
+    edge_vertex(C, e2a, e2b, o + 6);
+  }
+  if (cells) {
+    int32_t* c = cells + 4 * static_cast<size_t>(pos);
+    c[0] = C.gx;
+    c[1] = C.gy;
+    c[2] = C.gz;
+    c[3] = tag;
+  }
+}
+
+__device__ __forceinline__ int tet_mask(const CubeCorners& C, int t) {
+  int m = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) m |= (C.val[c_tets[t][k]] < 0.0f) ? (1 << k) : 0;
+  return m;
+}
+
+__global__ void __launch_bounds__(kExtractThreads)
+    extract_kernel(const __grid_constant__ VolumeArgs vol, float v, float* __restrict__ tris,
+                   int32_t* __restrict__ cells, unsigned int capacity,
+                   unsigned int* __restrict__ counter) {
+  __shared__ float s_val[9 * 9 * 9];
+  __shared__ int s_nb[8];
+  __shared__ int s_b[3];
+  __shared__ int s_skip;
+  const unsigned int c = *reinterpret_cast<volatile unsigned int*>(&vol.hdr->count);
+  const unsigned int units = vol.slot_index ? vol.slots : (c < vol.pool ? c : vol.pool);
+  const unsigned lane = threadIdx.x & 31u;
+  for (unsigned int unit = blockIdx.x; unit < units; unit += gridDim.x) {
+    if (threadIdx.x == 0) {
+      int bx = 0, by = 0, bz = 0, skip = 0;
+      if (vol.slot_index) {
+        const unsigned long long key = vol.table[unit].key;
+        skip = key == kEmptyKey;
+        if (!skip) unpack_key(key, bx, by, bz);
+      } else {
+        bx = vol.coords[3 * static_cast<size_t>(unit)];
+        by = vol.coords[3 * static_cast<size_t>(unit) + 1];
+        bz = vol.coords[3 * static_cast<size_t>(unit) + 2];
+      }
+      s_skip = skip;
+      s_b[0] = bx;
+      s_b[1] = by;
+      s_b[2] = bz;
+    }
+    __syncthreads();
+    if (s_skip) {  // uniform across the CTA
+      __syncthreads();
+      continue;
+    }
+    const int bx = s_b[0], by = s_b[1], bz = s_b[2];
+    if (threadIdx.x < 8) {
+      const int d = threadIdx.x;
+      int idx = static_cast<int>(unit);
+      if (d) {
+        const int nx = bx + (d & 1), ny = by + ((d >> 1) & 1), nz = bz + ((d >> 2) & 1);
+        // neighbours beyond the key range are absent
+        const bool in_range = nx < kKeyBias && ny < kKeyBias && nz < kKeyBias;
+        idx = in_range ? lookup_block(vol, pack_key(nx, ny, nz), nx, ny, nz) : kAbsent;
+      }
+      s_nb[d] = idx >= 0 ? idx : -1;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 9 * 9 * 9; i += kExtractThreads) {
+      const int x = i % 9, y = (i / 9) % 9, z = i / 81;
+      const int idx = s_nb[(x >> 3) | ((y >> 3) << 1) | ((z >> 3) << 2)];
+      float m = __int_as_float(0x7fc00000);  // NaN: unobserved
+      if (idx >= 0) {
+        const float4 sum = vol.twrg[static_cast<size_t>(idx) * kBlockVoxels +
+                                    local_index(x & 7, y & 7, z & 7)];
+        if (sum.y > 0.0f) m = __fdiv_rn(sum.x, sum.y);
+      }
+      s_val[i] = m;
+    }
+    __syncthreads();
+
+    CubeCorners C;
+    const int lx = threadIdx.x & 7, ly = (threadIdx.x >> 3) & 7, lz = threadIdx.x >> 6;
+    C.gx = bx * kBlockEdge + lx;
+    C.gy = by * kBlockEdge + ly;
+    C.gz = bz * kBlockEdge + lz;
+    C.v = v;
+    bool ok = true;
+    unsigned inside = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      C.val[k] = s_val[(lz + (k >> 2)) * 81 + (ly + ((k >> 1) & 1)) * 9 + lx + (k & 1)];
+      ok = ok && !isnan(C.val[k]);
+      inside |= (C.val[k] < 0.0f) ? (1u << k) : 0u;
+    }
+    int ntri = 0;
+    if (ok && inside != 0u && inside != 0xFFu) {
+#pragma unroll
+      for (int t = 0; t < 6; ++t) {
+        const int n_in = __popc(tet_mask(C, t));
+        ntri += (n_in == 0 || n_in == 4) ? 0 : (n_in == 2 ? 2 : 1);
+      }
+    }
+    // warp-wide exclusive scan of the counts, one reservation per warp
+    int incl = ntri;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (static_cast<int>(lane) >= o) incl += y;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    unsigned base = 0;
+    if (lane == 31 && total) base = atomicAdd(counter, static_cast<unsigned>(total));
+    base = __shfl_sync(0xffffffffu, base, 31);
+    unsigned pos = base + static_cast<unsigned>(incl - ntri);
+    if (ntri) {
+#pragma unroll 1
+      for (int t = 0; t < 6; ++t) {
+        const int m = tet_mask(C, t);
+        const int n_in = __popc(m);
+        if (n_in == 0 || n_in == 4) continue;
+        const unsigned char* T = c_tets[t];
+        if (n_in == 2) {
+          const unsigned char* o = c_pair[m];
+          const int a = T[o[0]], b = T[o[1]], cc = T[o[2]], d = T[o[3]];
+          write_triangle(C, a, cc, a, d, b, d, 2 * t, pos++, capacity, tris, cells);
+          write_triangle(C, a, cc, b, d, b, cc, 2 * t + 1, pos++, capacity, tris, cells);
+        } else {
+          const int lone = n_in == 1 ? m : (~m & 15);
+          const int i = __ffs(lone) - 1;
+          const unsigned char* o = c_lone[i];
+          const int a = T[o[0]], b = T[o[1]], cc = T[o[2]], d = T[o[3]];
+          if (n_in == 1)
+            write_triangle(C, a, b, a, cc, a, d, 2 * t, pos++, capacity, tris, cells);
+          else
+            write_triangle(C, a, b, a, d, a, cc, 2 * t, pos++, capacity, tris, cells);
+        }
+      }
+    }
+    __syncthreads();  // the tile is rewritten for the next block
+  }
+}
+
 static inline int tiles_of(int n) { return (n + kTile - 1) / kTile; }
 
 // ----------------------------------------------------------------------------
@@ -1112,6 +1307,16 @@ cudaError_t launch_clear_used(const VolumeArgs& vol, int sm_count, cudaStream_t 
     clear_slots_kernel<<<sm_count * 8, 256, 0, s>>>(vol);
   else
     clear_used_kernel<<<sm_count * 8, 256, 0, s>>>(vol);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_extract(const VolumeArgs& vol, float v, float* tris, int32_t* cells,
+                           unsigned int capacity, unsigned int* counter, int sm_count,
+                           cudaStream_t s) {
+  // persistent: a few CTAs of 512 threads per SM loop over the blocks
+  extract_kernel<<<sm_count * 4, kExtractThreads, 0, s>>>(vol, v, tris, cells, capacity,
+                                                         counter);
   note_launch();
   return cudaGetLastError();
 }

@@ -34,6 +34,12 @@ cudaError_t launch_slot_list(const VolumeArgs& vol, unsigned int* list, int32_t*
                              unsigned int cap, unsigned int* found, cudaStream_t s);
 // Zero the used pool blocks (before the table is cleared).
 cudaError_t launch_clear_used(const VolumeArgs& vol, int sm_count, cudaStream_t s);
+// Marching-tetrahedra surface of the volume: triangles (9 floats each) and
+// cell records (4 int32 each), either may be null; writes at most capacity of
+// them and adds the total to *counter (which the caller zeroes first).
+cudaError_t launch_extract(const VolumeArgs& vol, float v, float* tris, int32_t* cells,
+                           unsigned int capacity, unsigned int* counter, int sm_count,
+                           cudaStream_t s);
 // Accumulate table occupancy, probe lengths and the pool's total weight into
 // *out (which the caller zeroes first).
 cudaError_t launch_table_stats(const VolumeArgs& vol, TableStatsDev* out, int sm_count,

@@ -40,7 +40,8 @@ EXPORTED = ("tsdf_volume_bytes", "tsdf_volume_create", "tsdf_volume_create_in",
             "tsdf_server_create", "tsdf_server_destroy", "tsdf_server_clock",
             "tsdf_server_submit", "tsdf_server_poll", "tsdf_server_pending",
             "tsdf_server_replay", "tsdf_volume_table_stats", "tsdf_volume_copy",
-            "tsdf_autotune_frame", "tsdf_batch_autotune")
+            "tsdf_autotune_frame", "tsdf_batch_autotune", "tsdf_extract_mesh_async",
+            "tsdf_extract_mesh")
 
 
 class tsdf_intrinsics(ctypes.Structure):
@@ -74,6 +75,11 @@ class tsdf_tuning(ctypes.Structure):
                 ("ctas_per_sm", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("candidates", ctypes.c_int), ("best_ms", ctypes.c_float),
                 ("default_ms", ctypes.c_float)]
+
+
+class tsdf_extract_timing(ctypes.Structure):
+    _fields_ = [("compute_ms", ctypes.c_float), ("d2h_ms", ctypes.c_float),
+                ("d2h_bytes", ctypes.c_uint64)]
 
 
 class tsdf_frame(ctypes.Structure):
@@ -170,6 +176,10 @@ def lib() -> ctypes.CDLL:
                                         ctypes.POINTER(tsdf_completion)]),
             "tsdf_volume_table_stats": (st, [_P, _P, ctypes.POINTER(tsdf_table_stats)]),
             "tsdf_volume_copy": (st, [_P, _P, _P]),
+            "tsdf_extract_mesh_async": (st, [_P, _P, _P, ctypes.c_uint32, _P, _P]),
+            "tsdf_extract_mesh": (st, [_P, _P, _P, ctypes.c_uint32,
+                                       ctypes.POINTER(ctypes.c_uint32),
+                                       ctypes.POINTER(tsdf_extract_timing), _P]),
             "tsdf_autotune_frame": (st, [_P, _P, ctypes.c_int, ctypes.c_int,
                                          ctypes.POINTER(tsdf_intrinsics),
                                          ctypes.POINTER(tsdf_pose), _P, ctypes.c_int, _P,
@@ -377,6 +387,34 @@ def tsdf_volume_table_stats(vol, stream=None) -> dict:
 
 def tsdf_volume_copy(dst, src, stream=None) -> str:
     return _st(lib().tsdf_volume_copy(dst, src, _stream(stream)))
+
+
+def tsdf_extract_mesh_async(vol, triangles, cells, capacity, count, stream=None) -> str:
+    """Device buffers (torch tensors or addresses): triangles (cap, 9) float32,
+    cells (cap, 4) int32, count a uint32/int32 device scalar."""
+    return _st(lib().tsdf_extract_mesh_async(vol, _dptr(triangles), _dptr(cells), int(capacity),
+                                             _dptr(count), _stream(stream)))
+
+
+def tsdf_extract_mesh(vol, stream=None, cells=True):
+    """(triangles float32 (n,3,3), cells int32 (n,4) or None, timing dict)."""
+    n = ctypes.c_uint32()
+    st = _st(lib().tsdf_extract_mesh(vol, None, None, 0, ctypes.byref(n), None,
+                                     _stream(stream)))
+    if st != "OK":
+        raise TsdfError(st, "tsdf_extract_mesh")
+    tris = np.zeros((n.value, 3, 3), dtype=np.float32)
+    cel = np.zeros((n.value, 4), dtype=np.int32) if cells else None
+    t = tsdf_extract_timing()
+    if n.value:
+        m = ctypes.c_uint32()
+        st = _st(lib().tsdf_extract_mesh(vol, tris.ctypes.data, cel.ctypes.data if cells else None,
+                                         n.value, ctypes.byref(m), ctypes.byref(t),
+                                         _stream(stream)))
+        if st != "OK":
+            raise TsdfError(st, "tsdf_extract_mesh")
+    return tris, cel, {"compute_ms": float(t.compute_ms), "d2h_ms": float(t.d2h_ms),
+                       "d2h_bytes": int(t.d2h_bytes)}
 
 
 def _tuning(t):
@@ -611,6 +649,9 @@ class Volume:
     def autotune(self, depth, intr, pose, rgb=None, reps=5, stream=None):
         h, w = depth.shape[-2], depth.shape[-1]
         return tsdf_autotune_frame(self.handle, depth, w, h, intr, pose, rgb, reps, stream)
+
+    def extract_mesh(self, stream=None, cells=True):
+        return tsdf_extract_mesh(self.handle, stream, cells)
 
     def table_stats(self, stream=None) -> dict:
         return tsdf_volume_table_stats(self.handle, stream)
