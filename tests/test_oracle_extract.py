@@ -69,6 +69,26 @@ def test_one_outside_corner_flips_normals():
     assert np.all(np.einsum("ij,ij->i", normals(tris), mid - 0.05) < 0)
 
 
+def test_a_zero_corner_is_outside():
+    """E3: inside means < 0. A corner at exactly 0 among positive corners makes
+    no surface; among negative ones it is the lone outside corner, and its
+    triangles meet at its own centre (t = 1 on every edge towards it)."""
+    ov = volume()
+    for x in range(2):
+        for y in range(2):
+            for z in range(2):
+                ov.set_voxel(x, y, z, 0.0 if (x, y, z) == (0, 0, 0) else 0.5)
+    assert len(ov.extract()[0]) == 0
+    ov = volume()
+    for x in range(2):
+        for y in range(2):
+            for z in range(2):
+                ov.set_voxel(x, y, z, 0.0 if (x, y, z) == (1, 1, 1) else -0.5)
+    tris, _ = ov.extract()
+    assert len(tris) == 6
+    assert np.allclose(tris, 0.15)
+
+
 def test_unobserved_corner_removes_the_cube():
     ov = volume()
     for x in range(2):
