@@ -4,13 +4,13 @@
 truncation 2 cm, 2^20 table slots, 2^18 pool blocks).
 
 One step = one pass of the whole hot path (allocate + integrate, paper
-Section 2.2) over one frame through tsdf_fuse_frame_async, into a freshly
-reset volume (so allocation never degenerates into a lookup-only pass,
-Section 4.2). Between steps, outside the timed events, the volume is reset and
-L2 is scrubbed (512 MB write, then 512 MB read). Each step is timed with CUDA
-events on the launching stream. The same frames are also run as the two
-separate stages (stage A, then stage B), each with its own events, for the
-per-stage rooflines.
+Section 2.2) over one frame through tsdf_fuse_frame_async -- by default the
+fused tile kernel -- into a freshly reset volume (so allocation never
+degenerates into a lookup-only pass, Section 4.2). Between steps, outside the
+timed events, the volume is reset and L2 is scrubbed (512 MB write, then
+512 MB read). Each step is timed with CUDA events on the launching stream. The
+same frames are also run as the two separate stages (stage A, then stage B),
+each with its own events, for the per-stage rooflines.
 
 Prints ONE JSON line. With --impl reference the CPU oracle (single thread,
 host cores) is timed on the same workload instead.
@@ -179,7 +179,7 @@ def committed_traffic(kernel):
 # the GPU arm
 # ----------------------------------------------------------------------------
 def vol_fuse_mode(vol):
-    return getattr(vol, "_fuse_mode", 0)
+    return getattr(vol, "_fuse_mode", 2)
 
 
 def run_gpu(args, rank, world, local_rank):
@@ -199,7 +199,7 @@ def run_gpu(args, rank, world, local_rank):
                  ("allocate_mode", args.allocate_mode), ("fuse_mode", args.fuse_mode)):
         if x is not None:
             assert vol.set_option(k, x) == "OK"
-    vol._fuse_mode = 0 if args.fuse_mode is None else args.fuse_mode
+    vol._fuse_mode = 2 if args.fuse_mode is None else args.fuse_mode
     stream = torch.cuda.Stream()
     sp = stream.cuda_stream
     dev = [(torch.from_numpy(f.depth).cuda(), torch.from_numpy(f.rgb).cuda()) for f in frames]
@@ -293,7 +293,7 @@ def run_gpu(args, rank, world, local_rank):
     step_mean = total_ms / args.steps
     a_gbs, b_gbs = a_bytes / (a_ms * 1e6), b_bytes / (b_ms * 1e6)
     f_gbs = f_bytes / (step_mean * 1e6)
-    fused = vol_fuse_mode(vol) == 1
+    fused = vol_fuse_mode(vol) != 0
     if fused:
         dom = ("fused", f_bytes, step_mean, f_gbs, "fuse_kernel")
     elif b_ms >= a_ms:
@@ -317,7 +317,7 @@ def run_gpu(args, rank, world, local_rank):
         # back to the configuration the headline timed
         for k, x, default in (("allocate_mode", args.allocate_mode, 1),
                               ("integrate_mode", args.integrate_mode, 0),
-                              ("fuse_mode", args.fuse_mode, 0),
+                              ("fuse_mode", args.fuse_mode, 2),
                               ("probe_load", args.probe_load, 0)):
             assert vol.set_option(k, default if x is None else x) == "OK"
 
@@ -592,13 +592,14 @@ def run_load_sweep(args, torch, tsdf, rendered):
 
     fill, snap, work = vol(), vol(), vol()
     kfill, ksnap, kwork = vol(slot_index=1), vol(slot_index=1), vol(slot_index=1)
-    bfill = vol(probe_bound=SWEEP_BOUND, allocate_mode=0, integrate_mode=0)
+    bfill = vol(probe_bound=SWEEP_BOUND, fuse_mode=0, allocate_mode=0, integrate_mode=0)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     scrub = torch.ones(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    variants = (("tile+scatter", work, snap, dict(allocate_mode=1, integrate_mode=0, fuse_mode=0)),
+    variants = (("fused_tile", work, snap, dict(fuse_mode=2)),
+                ("tile+scatter", work, snap, dict(allocate_mode=1, integrate_mode=0, fuse_mode=0)),
                 ("paper_protocol", work, snap, dict(allocate_mode=0, integrate_mode=0, fuse_mode=0)),
                 ("fused_warp", work, snap, dict(fuse_mode=1)),
-                ("slot_index", kwork, ksnap, dict(allocate_mode=1, integrate_mode=0, fuse_mode=0)))
+                ("slot_index", kwork, ksnap, dict(fuse_mode=2)))
 
     def fuse(v, fr):
         d, c, intr, pose, _ = fr

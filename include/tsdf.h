@@ -137,10 +137,15 @@ typedef enum tsdf_option {
    * index, and the kernel boundary publishes every index before stage B. */
   TSDF_OPT_ALLOCATE_MODE = 4,
   /* What tsdf_fuse_frame* launch: 0 = stage A then stage B (two kernels,
-   * Section 2.2, default); 1 = one fused kernel per frame in which each warp
-   * walks its points once, inserts its distinct blocks (waiting, bounded, for
-   * indices published by others) and adds its sums. Results are identical up
-   * to the order of floating-point additions. */
+   * Section 2.2, with the strategies above); 1 = one fused kernel in which
+   * each warp walks its points once, inserts its distinct blocks (waiting,
+   * bounded, for indices published by others) and adds its sums; 2 = one
+   * fused kernel per 16x16 pixel tile (default): the walk runs once, the
+   * tile's distinct blocks are inserted warp-cooperatively and their indices
+   * kept in shared memory, then every accepted voxel's sums are added with
+   * no further table probe. Results are identical up to the order of
+   * floating-point additions. Safe without a grid barrier because a point
+   * only touches blocks whose indices it has resolved. */
   TSDF_OPT_FUSE_MODE = 5,
   /* Batches only: cap on resident CTAs per SM of the persistent batched
    * kernels (0 = as many as fit, default). */
@@ -307,7 +312,8 @@ tsdf_status tsdf_batch_create(int max_frames, tsdf_batch** out);
 void tsdf_batch_destroy(tsdf_batch* batch);
 
 /* TSDF_OPT_PROBE_LOAD, TSDF_OPT_ALLOCATE_MODE (1 or 2), TSDF_OPT_INTEGRATE_MODE,
- * TSDF_OPT_FUSE_MODE, TSDF_OPT_CTAS_PER_SM, TSDF_OPT_USE_GRAPH. */
+ * TSDF_OPT_FUSE_MODE (default 2, as for volumes), TSDF_OPT_CTAS_PER_SM,
+ * TSDF_OPT_USE_GRAPH. */
 tsdf_status tsdf_batch_set_option(tsdf_batch* batch, tsdf_option opt, int64_t value);
 
 /* Enqueue the fusion of n frames (1 <= n <= max_frames), each into a distinct

@@ -37,7 +37,7 @@ struct tsdf_batch {
   unsigned* status_dev = nullptr;
   unsigned* status_host = nullptr;
   // configuration
-  int probe_load = 0, allocate_mode = 1, integrate_mode = 0, fuse_mode = 0, factor = 0;
+  int probe_load = 0, allocate_mode = 1, integrate_mode = 0, fuse_mode = 2, factor = 0;
   int use_graph = 0;
   cudaStream_t capture = nullptr;
   cudaGraphExec_t exec[2] = {nullptr, nullptr};
@@ -137,7 +137,7 @@ tsdf_status tsdf_batch_set_option(tsdf_batch* b, tsdf_option opt, int64_t value)
       b->integrate_mode = static_cast<int>(value);
       return TSDF_OK;
     case TSDF_OPT_FUSE_MODE:
-      if (value < 0 || value > 1) return TSDF_ERR_INVALID_ARG;
+      if (value < 0 || value > 2) return TSDF_ERR_INVALID_ARG;
       b->fuse_mode = static_cast<int>(value);
       return TSDF_OK;
     case TSDF_OPT_CTAS_PER_SM:

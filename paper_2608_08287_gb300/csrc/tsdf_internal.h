@@ -44,7 +44,7 @@ struct tsdf_volume {
   int probe_load = tsdf::kLoadCached;
   int allocate_mode = 1;
   int integrate_mode = 0;
-  int fuse_mode = 0;
+  int fuse_mode = 2;
   int threads = 256;
   void* stage = nullptr;
   size_t stage_bytes = 0;

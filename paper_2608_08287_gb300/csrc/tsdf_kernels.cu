@@ -241,6 +241,27 @@ __device__ __forceinline__ bool tile_ray(const FrameArgs& f, int tile, int tiles
   return make_ray(f, u, v, __ldg(f.depth + v * f.W + u), r);
 }
 
+// Each point's first three distinct blocks into the tile's key list, after a
+// per-warp __match_any_sync dedupe. Every lane of the warp calls it.
+template <int Op, int P>
+__device__ __forceinline__ void tile_list_point_keys(TileShared& T, const VolumeArgs& vol,
+                                                     const PointKeys& pk) {
+  const unsigned lane = threadIdx.x & 31u;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const unsigned long long key = j == 0 ? pk.k0 : (j == 1 ? pk.k1 : pk.k2);
+    const bool has = pk.n > j;
+    const unsigned m = __ballot_sync(0xffffffffu, has);
+    if (has) {
+      const unsigned peers = __match_any_sync(m, key);
+      if (lane == static_cast<unsigned>(__ffs(peers) - 1)) {
+        // a key that cannot be listed is inserted by its adder at once
+        if (tile_add(T, key) == -1) resolve_single<Op, P>(vol, key);
+      }
+    }
+  }
+}
+
 // Phases 1 and 2 of every tile kernel: the point's walk and its distinct
 // accepted blocks; a per-warp __match_any_sync dedupe of each point's first
 // three blocks before the tile set; then each warp resolves the keys it
@@ -277,20 +298,7 @@ __device__ __forceinline__ void tile_collect(TileShared& T, const FrameArgs& f,
       }
     }
   }
-  const unsigned lane = threadIdx.x & 31u;
-#pragma unroll
-  for (int j = 0; j < 3; ++j) {
-    const unsigned long long key = j == 0 ? pk.k0 : (j == 1 ? pk.k1 : pk.k2);
-    const bool has = pk.n > j;
-    const unsigned m = __ballot_sync(0xffffffffu, has);
-    if (has) {
-      const unsigned peers = __match_any_sync(m, key);
-      if (lane == static_cast<unsigned>(__ffs(peers) - 1)) {
-        // a key that cannot be listed is inserted by its adder at once
-        if (tile_add(T, key) == -1) resolve_single<Op, P>(vol, key);
-      }
-    }
-  }
+  tile_list_point_keys<Op, P>(T, vol, pk);
 }
 
 // Five sums of one accepted voxel, added straight to the pool.
@@ -338,6 +346,160 @@ __global__ void __launch_bounds__(kThreads)
                          const __grid_constant__ VolumeArgs vol, int tiles_x) {
   __shared__ TileShared T;
   tile_allocate_body<P, M>(T, f, vol, blockIdx.x, tiles_x);
+}
+
+// ----------------------------------------------------------------------------
+// fused, tile strategy: one walk per point, both stages in one kernel
+// ----------------------------------------------------------------------------
+// Phase 1 is stage A's tile collection (walk, distinct keys, shared set and
+// list). Phase 2 inserts the list warp-cooperatively and OBTAINS each key's
+// pool index (a key won by another CTA may still be unpublished: that wait
+// is bounded, and a winner never waits before publishing, so it cannot
+// deadlock). Phase 3 adds every accepted voxel's sums, taking its block's
+// index from the tile list in shared memory: no table probe at all, and the
+// walk is not repeated. Safe without a grid barrier because a point only
+// touches blocks whose indices it has resolved.
+struct FusedTileShared {
+  TileShared T;
+  int idx[kTileList];
+};
+
+// A sample of the fused tile kernel packed in one word: accepted flag, the
+// block's offset from the point's first accepted block (4 bits per axis,
+// biased by 8: a band of at most 2*16+1 samples, one voxel apart, crosses at
+// most four block boundaries per axis) and the voxel's local index.
+constexpr unsigned kSampleValid = 1u << 31;
+
+__device__ __forceinline__ unsigned pack_sample(int dbx, int dby, int dbz, int l) {
+  return kSampleValid | (static_cast<unsigned>(dbx + 8) << 9) |
+         (static_cast<unsigned>(dby + 8) << 13) | (static_cast<unsigned>(dbz + 8) << 17) |
+         static_cast<unsigned>(l);
+}
+
+template <int P, int M>
+__device__ __forceinline__ void tile_fused_body(FusedTileShared& S, const FrameArgs& f,
+                                                const VolumeArgs& vol, int tile, int tiles_x) {
+  TileShared& T = S.T;
+  tile_init(T, vol);
+  __syncthreads();
+  if (T.err) {  // poisoned volume: do nothing (uniform across the CTA)
+    __syncthreads();
+    return;
+  }
+  Ray r;
+  int u, v;
+  const bool valid = tile_ray(f, tile, tiles_x, r, u, v);
+  PointKeys pk;
+  // phase 1: the walk and the tile's key list. With the half band compiled,
+  // each accepted sample is reduced to one packed word and its tsdf value,
+  // so little state is held across the barriers.
+  constexpr int K = M > 0 ? 2 * M + 1 : 1;
+  unsigned smp[K];
+  float tv[K];
+  int bx0 = 0, by0 = 0, bz0 = 0;
+  if constexpr (M > 0) {
+    unsigned acc = 0;
+    Walk<M> w;
+    if (valid) acc = walk_point<M>(f, r, w);
+    bool first = true;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      smp[k] = 0u;
+      tv[k] = 0.0f;
+      if ((acc >> k) & 1u) {
+        const int bx = w.gx[k] >> 3, by = w.gy[k] >> 3, bz = w.gz[k] >> 3;
+        if (first) {
+          bx0 = bx;
+          by0 = by;
+          bz0 = bz;
+          first = false;
+        }
+        smp[k] = pack_sample(bx - bx0, by - by0, bz - bz0, local_index(w.gx[k], w.gy[k], w.gz[k]));
+        tv[k] = tsdf_value(f, r.d, w.zc[k]);
+        point_key<kOpFused, P>(pk, pack_key(bx, by, bz), T, vol);
+      }
+    }
+    tile_list_point_keys<kOpFused, P>(T, vol, pk);
+  } else {
+    Walk<M> w;
+    unsigned acc;
+    tile_collect<kOpFused, P, M>(T, f, vol, r, valid, w, acc, pk);
+  }
+  __syncthreads();
+  // phase 2: insert the list and obtain the indices
+  const int n = T.n < kTileList ? T.n : kTileList;
+  const unsigned lane = threadIdx.x & 31u;
+  for (int base = (threadIdx.x & ~31); base < n; base += kThreads) {
+    const int i = base + static_cast<int>(lane);
+    const bool has = i < n;
+    const int res = warp_insert_get<P>(vol, has ? T.list[i] : kEmptyKey, has);
+    if (has) S.idx[i] = res;
+  }
+  __syncthreads();
+  if (!valid) return;  // no barrier follows
+
+  // phase 3: the sums, each block's index from the tile list
+  float cr = 0.0f, cg = 0.0f, cb = 0.0f;
+  const bool colour = f.rgb != nullptr;
+  if (colour) {
+    const uint8_t* c = f.rgb + 3 * (static_cast<size_t>(v) * f.W + u);
+    cr = static_cast<float>(c[0]);
+    cg = static_cast<float>(c[1]);
+    cb = static_cast<float>(c[2]);
+  }
+  // a key missing from the list (set or list full) is resolved on its own
+  auto index_of = [&](unsigned long long key) -> int {
+    const int p = tile_find(T, key);
+    return p >= 0 ? S.idx[p] : resolve_single<kOpFused, P>(vol, key);
+  };
+  BlockCacheT bc;
+  if constexpr (M > 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const unsigned q = smp[k];
+      if (!(q & kSampleValid)) continue;
+      const unsigned long long key =
+          pack_key(bx0 + static_cast<int>((q >> 9) & 15u) - 8,
+                   by0 + static_cast<int>((q >> 13) & 15u) - 8,
+                   bz0 + static_cast<int>((q >> 17) & 15u) - 8);
+      if (key != bc.key) {
+        bc.key = key;
+        bc.idx = index_of(key);
+      }
+      if (bc.idx >= 0)
+        add_contribution(vol.twrg, vol.blue,
+                         static_cast<size_t>(bc.idx) * kBlockVoxels + (q & 511u), tv[k], colour,
+                         cr, cg, cb);
+    }
+  } else {
+    WalkDedupe walk;
+    for (int k = 0; k <= 2 * f.M; ++k) {
+      int gx, gy, gz;
+      float zc;
+      if (!sample_voxel(f, r, k, gx, gy, gz) || walk.seen_then_push(gx, gy, gz) ||
+          !voxel_test(f, gx, gy, gz, zc))
+        continue;
+      const unsigned long long key = block_key_of(gx, gy, gz);
+      if (key != bc.key) {
+        bc.key = key;
+        bc.idx = index_of(key);
+      }
+      if (bc.idx >= 0)
+        add_contribution(vol.twrg, vol.blue,
+                         static_cast<size_t>(bc.idx) * kBlockVoxels + local_index(gx, gy, gz),
+                         tsdf_value(f, r.d, zc), colour, cr, cg, cb);
+    }
+  }
+}
+
+// Four CTAs per SM: the register cap costs a few spilled words in the walk
+// and measured faster than three CTAs without spills.
+template <int P, int M>
+__global__ void __launch_bounds__(kThreads, 4)
+    tile_fused_kernel(const __grid_constant__ FrameArgs f, const __grid_constant__ VolumeArgs vol,
+                      int tiles_x) {
+  __shared__ FusedTileShared S;
+  tile_fused_body<P, M>(S, f, vol, blockIdx.x, tiles_x);
 }
 
 // ----------------------------------------------------------------------------
@@ -1083,6 +1245,33 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
+template <int P>
+__global__ void __launch_bounds__(kThreads, 4)
+    batch_tile_fused_kernel(const BatchHeader* __restrict__ table) {
+  __shared__ FusedTileShared S;
+  __shared__ SessionArgs sa;
+  __shared__ int s_sess;
+  const int n = table->n;
+  const int total = table->total_tiles;
+  const SessionArgs* Sa = reinterpret_cast<const SessionArgs*>(table + 1);
+  int cur = -1;
+  for (int tile = blockIdx.x; tile < total; tile += gridDim.x) {
+    if (threadIdx.x == 0) s_sess = find_session(Sa, n, tile);
+    __syncthreads();
+    const int s = s_sess;
+    if (s != cur) {
+      load_session(sa, Sa + s);
+      cur = s;
+    }
+    __syncthreads();
+    if (sa.f.M == 4)
+      tile_fused_body<P, 4>(S, sa.f, sa.vol, tile - sa.tile_begin, sa.tiles_x);
+    else
+      tile_fused_body<P, 0>(S, sa.f, sa.vol, tile - sa.tile_begin, sa.tiles_x);
+    __syncthreads();  // S, sa and s_sess are rewritten for the next tile
+  }
+}
+
 // Kind: kBatchScatter (stage B, paper's update), or a warp_body operation.
 constexpr int kBatchScatter = 10;
 
@@ -1195,10 +1384,37 @@ cudaError_t launch_integrate(const FrameArgs& f, const VolumeArgs& vol, int mode
   return e;
 }
 
+template <int P, int M>
+static cudaError_t launch_tile_fused_kernel(const FrameArgs& f, const VolumeArgs& vol,
+                                            cudaStream_t s) {
+  const int tx = tiles_of(f.W);
+  tile_fused_kernel<P, M><<<tx * tiles_of(f.H), kThreads, 0, s>>>(f, vol, tx);
+  return cudaGetLastError();
+}
+
+template <int P>
+static cudaError_t launch_tile_fused_m(const FrameArgs& f, const VolumeArgs& vol,
+                                       cudaStream_t s) {
+  switch (f.M) {
+    case 2: return launch_tile_fused_kernel<P, 2>(f, vol, s);
+    case 4: return launch_tile_fused_kernel<P, 4>(f, vol, s);
+    case 8: return launch_tile_fused_kernel<P, 8>(f, vol, s);
+    default: return launch_tile_fused_kernel<P, 0>(f, vol, s);
+  }
+}
+
 cudaError_t launch_fused(const FrameArgs& f, const VolumeArgs& vol, int probe_load, int mode,
                          cudaStream_t s) {
-  (void)mode;
-  const cudaError_t e = launch_warp_p<kOpFused>(f, vol, probe_load, s);
+  cudaError_t e;
+  if (mode == 2) {
+    switch (probe_load) {
+      case kLoadL2: e = launch_tile_fused_m<kLoadL2>(f, vol, s); break;
+      case kLoadRelaxed: e = launch_tile_fused_m<kLoadRelaxed>(f, vol, s); break;
+      default: e = launch_tile_fused_m<kLoadCached>(f, vol, s); break;
+    }
+  } else {
+    e = launch_warp_p<kOpFused>(f, vol, probe_load, s);
+  }
   note_launch();
   return e;
 }
@@ -1239,6 +1455,15 @@ cudaError_t launch_batch(const BatchHeader* table, int probe_load, int allocate_
                          int integrate_mode, int fuse_mode, int factor, int grid_limit,
                          cudaStream_t s) {
   cudaError_t e;
+  if (fuse_mode == 2) {
+    switch (probe_load) {
+      case kLoadL2: return launch_persistent(batch_tile_fused_kernel<kLoadL2>, table, factor, grid_limit, s);
+      case kLoadRelaxed:
+        return launch_persistent(batch_tile_fused_kernel<kLoadRelaxed>, table, factor, grid_limit, s);
+      default:
+        return launch_persistent(batch_tile_fused_kernel<kLoadCached>, table, factor, grid_limit, s);
+    }
+  }
   if (fuse_mode == 1) {
     switch (probe_load) {
       case kLoadL2: return launch_persistent(batch_point_kernel<kOpFused, kLoadL2>, table, factor, grid_limit, s);

@@ -121,16 +121,15 @@ tsdf_status tsdf_autotune_frame(tsdf_volume* vol, const float* depth_dev, int wi
   if (e == cudaSuccess) e = ev.init();
   if (st == TSDF_OK && e != cudaSuccess) st = tsdf::from_cuda(e);
 
-  // the default first, then the other stage A x stage B pairs, the fused
-  // kernel, and the other probe loads of the default stage A
-  const Config dflt{1, 0, 0, 0, 0, 0};
+  // the default (fused tile kernel) first, then every stage A x stage B
+  // pair, the fused warp kernel, and the other probe loads of the default
+  const Config dflt{1, 0, 2, 0, 0, 0};
   std::vector<Config> cands{dflt};
   for (int a = 0; a <= 2; ++a)
-    for (int i = 0; i <= 1; ++i)
-      if (!(a == 1 && i == 0)) cands.push_back({a, i, 0, 0, 0, 0});
+    for (int i = 0; i <= 1; ++i) cands.push_back({a, i, 0, 0, 0, 0});
   cands.push_back({1, 0, 1, 0, 0, 0});
-  cands.push_back({1, 0, 0, 1, 0, 0});
-  cands.push_back({1, 0, 0, 2, 0, 0});
+  cands.push_back({1, 0, 2, 1, 0, 0});
+  cands.push_back({1, 0, 2, 2, 0, 0});
 
   std::vector<float> times;
   for (size_t c = 0; c < cands.size() && st == TSDF_OK; ++c) {
@@ -208,7 +207,7 @@ tsdf_status tsdf_batch_autotune(tsdf_batch* batch, const tsdf_frame* frames, int
   };
 
   int tried = 0;
-  const Config dflt{1, 0, 0, 0, 0, 1};
+  const Config dflt{1, 0, 2, 0, 0, 1};
   Config best = dflt;
   float best_ms = 0.0f, dflt_ms = 0.0f;
   if (st == TSDF_OK) st = run(dflt, &dflt_ms);
@@ -225,6 +224,7 @@ tsdf_status tsdf_batch_autotune(tsdf_batch* batch, const tsdf_frame* frames, int
     }
   };
   // stage 1: strategies (the batched kernels take stage A strategies 1 and 2)
+  consider({1, 0, 0, 0, 0, 1});
   consider({1, 1, 0, 0, 0, 1});
   consider({2, 0, 0, 0, 0, 1});
   consider({2, 1, 0, 0, 0, 1});

@@ -36,12 +36,12 @@ def frame(k, w=160, h=120):
 
 def check_tuning(t, batch):
     assert t["allocate_mode"] in ((1, 2) if batch else (0, 1, 2))
-    assert t["integrate_mode"] in (0, 1) and t["fuse_mode"] in (0, 1)
+    assert t["integrate_mode"] in (0, 1) and t["fuse_mode"] in (0, 1, 2)
     assert t["probe_load"] in (0, 1, 2)
     if batch:
         assert 0 <= t["ctas_per_sm"] <= 4 and t["use_graph"] in (0, 1)
     assert 0 < t["best_ms"] <= t["default_ms"]
-    assert t["candidates"] >= 9
+    assert t["candidates"] >= 10
 
 
 def test_autotune_frame_keeps_the_volume_and_applies_the_choice():

@@ -84,8 +84,9 @@ def run_single(ss, rounds):
     return vols
 
 
-@pytest.mark.parametrize("opts", [dict(), dict(allocate_mode=2), dict(integrate_mode=1),
-                                  dict(fuse_mode=1), dict(use_graph=1),
+@pytest.mark.parametrize("opts", [dict(), dict(fuse_mode=0), dict(fuse_mode=0, allocate_mode=2),
+                                  dict(fuse_mode=0, integrate_mode=1), dict(fuse_mode=1),
+                                  dict(use_graph=1), dict(use_graph=1, fuse_mode=0),
                                   dict(use_graph=1, fuse_mode=1, ctas_per_sm=2)])
 def test_batch_equals_single_frame_path(opts):
     ss = sessions(9)

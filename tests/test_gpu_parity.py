@@ -104,7 +104,8 @@ BANDS = [(0.05, 0.2), (0.1, 0.3), (0.03, 0.12), (0.02, 0.1), (0.04, 0.08), (0.01
 
 # (fuse, allocate, integrate) modes: the fused kernel, and the two-stage path
 # with each stage A and stage B strategy
-MODES = [dict(fuse_mode=1),
+MODES = [dict(fuse_mode=2),
+         dict(fuse_mode=1),
          dict(fuse_mode=0, allocate_mode=2, integrate_mode=1),
          dict(fuse_mode=0, allocate_mode=1, integrate_mode=1),
          dict(fuse_mode=0, allocate_mode=0, integrate_mode=0),

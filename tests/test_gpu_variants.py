@@ -154,7 +154,7 @@ def test_bounded_probe_negative_control(orbit):
     frames, statuses, counts, ref = orbit
     lost_at = {}
     for bound in (8, 0):
-        gv = volume(probe_bound=bound, allocate_mode=0, integrate_mode=0)
+        gv = volume(probe_bound=bound, fuse_mode=0, allocate_mode=0, integrate_mode=0)
         for k in range(N_HIGH):
             d, c = to_dev(frames[k])
             assert gv.fuse(d, frames[k].intr, frames[k].pose, c) == "OK"   # always silent
