@@ -422,6 +422,22 @@ def run_extraction(args, vol, frames, dev, tsdf, sp, hbm):
             "call": "tsdf_extract_mesh (triangles only, pageable host buffer)"}
 
 
+def run_extraction_only(args):
+    import torch
+    from paper_2608_08287_gb300 import synth, tsdf
+    from paper_2608_08287_gb300.build import build_library
+    build_library()
+    spec = synth.ROOM_640
+    frames = make_frames(0)
+    vol = tsdf.Volume(spec.voxel_size, spec.truncation, spec.table_slots, spec.pool_blocks)
+    stream = torch.cuda.Stream()
+    dev = [(torch.from_numpy(f.depth).cuda(), torch.from_numpy(f.rgb).cuda()) for f in frames]
+    hbm, _ = peaks()
+    out = run_extraction(args, vol, frames, dev, tsdf, stream.cuda_stream, hbm)
+    vol.close()
+    return {"extraction": out}
+
+
 def run_e2e(args, vol, frames, torch, tsdf, sp, stream, flush, scrub, world=1):
     """Same metric through tsdf_fuse_frame_host: pinned host depth + colour are
     copied in, both stages run, the status word is read back, every step."""
@@ -749,6 +765,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--headline-only", action="store_true",
                     help="skip the batched and serving measurements")
+    ap.add_argument("--extraction-only", action="store_true",
+                    help="only fuse the bench frames and time surface extraction "
+                         "(a small command for profiling the extraction kernel)")
     ap.add_argument("--batch-steps", type=int, default=20)
     ap.add_argument("--clock-ms", type=int, default=100,
                     help="nvidia-smi sampling interval during the timed region")
@@ -773,6 +792,10 @@ def main():
             print(json.dumps(run_reference(args)), flush=True)
         return
 
+    if args.extraction_only:
+        if rank == 0:
+            print(json.dumps(run_extraction_only(args)), flush=True)
+        return
     if world > 1:
         import torch
         torch.cuda.set_device(local_rank)

@@ -465,9 +465,10 @@ typedef struct tsdf_extract_timing {
 } tsdf_extract_timing;
 
 /* Enqueue the extraction into device buffers: at most `capacity` triangles
- * and cell records are written (either pointer may be NULL), and *count_dev
- * (device) receives the total number of triangles, which may exceed
- * capacity. Nothing is allocated; nothing waits. */
+ * and cell records are written (either pointer may be NULL; cells_dev must be
+ * 16-byte aligned, TSDF_ERR_INVALID_ARG otherwise), and *count_dev (device)
+ * receives the total number of triangles, which may exceed capacity.
+ * Nothing is allocated; nothing waits. */
 tsdf_status tsdf_extract_mesh_async(tsdf_volume* vol, float* triangles_dev, int32_t* cells_dev,
                                     uint32_t capacity, uint32_t* count_dev, void* stream);
 

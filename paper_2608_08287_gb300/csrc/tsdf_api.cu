@@ -478,6 +478,10 @@ tsdf_status tsdf_extract_mesh_async(tsdf_volume* vol, float* triangles_dev, int3
                                     uint32_t capacity, uint32_t* count_dev, void* stream) {
   if (!vol || !count_dev) return TSDF_ERR_INVALID_ARG;
   if (capacity && !triangles_dev && !cells_dev) return TSDF_ERR_INVALID_ARG;
+  if ((reinterpret_cast<uintptr_t>(triangles_dev) % alignof(float)) != 0 ||
+      (reinterpret_cast<uintptr_t>(cells_dev) % 16) != 0 ||
+      (reinterpret_cast<uintptr_t>(count_dev) % alignof(uint32_t)) != 0)
+    return TSDF_ERR_INVALID_ARG;
   cudaStream_t s = as_stream(stream);
   cudaError_t e = cudaMemsetAsync(count_dev, 0, sizeof(uint32_t), s);
   if (e == cudaSuccess)

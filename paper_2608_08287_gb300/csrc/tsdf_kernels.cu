@@ -34,13 +34,15 @@ constexpr int kSetSlots = 2048;    // allocate_kernel: per-CTA key set (16 KB)
 constexpr int kTileSet = 1024;     // tile kernel: key set slots (8 KB)
 constexpr int kTileList = 768;     // tile kernel: compact key list (6 KB)
 
+// Pixel of this thread in tile `tile`: a tile is 16 pixels wide and
+// blockDim.x / 16 rows high; warp w covers the 8x4 patch (w & 1, w >> 1).
 __device__ __forceinline__ void tile_pixel(int tile, int tiles_x, int& u, int& v) {
   const int tx = tile % tiles_x;
   const int ty = tile / tiles_x;
   const int w = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   u = tx * kTile + (w & 1) * 8 + (lane & 7);
-  v = ty * kTile + (w >> 1) * 4 + (lane >> 3);
+  v = ty * static_cast<int>(blockDim.x >> 4) + (w >> 1) * 4 + (lane >> 3);
 }
 
 // Insert into the CTA's shared-memory key set; false if the set is full.
@@ -231,7 +233,7 @@ __device__ __forceinline__ void tile_init(TileShared& T, const VolumeArgs& vol) 
     T.err = load_err_volatile(vol.hdr);
     T.n = 0;
   }
-  for (int i = threadIdx.x; i < kTileSet; i += kThreads) T.set[i] = kEmptyKey;
+  for (int i = threadIdx.x; i < kTileSet; i += blockDim.x) T.set[i] = kEmptyKey;
 }
 
 __device__ __forceinline__ bool tile_ray(const FrameArgs& f, int tile, int tiles_x, Ray& r, int& u,
@@ -429,7 +431,7 @@ __device__ __forceinline__ void tile_fused_body(FusedTileShared& S, const FrameA
   // phase 2: insert the list and obtain the indices
   const int n = T.n < kTileList ? T.n : kTileList;
   const unsigned lane = threadIdx.x & 31u;
-  for (int base = (threadIdx.x & ~31); base < n; base += kThreads) {
+  for (int base = (threadIdx.x & ~31); base < n; base += blockDim.x) {
     const int i = base + static_cast<int>(lane);
     const bool has = i < n;
     const int res = warp_insert_get<P>(vol, has ? T.list[i] : kEmptyKey, has);
@@ -492,8 +494,9 @@ __device__ __forceinline__ void tile_fused_body(FusedTileShared& S, const FrameA
   }
 }
 
-// Four CTAs per SM: the register cap costs a few spilled words in the walk
-// and measured faster than three CTAs without spills.
+// 64 registers a thread (four 256-thread CTAs per SM): the cap costs a few
+// spilled words in the walk and measured faster than three CTAs without
+// spills.
 template <int P, int M>
 __global__ void __launch_bounds__(kThreads, 4)
     tile_fused_kernel(const __grid_constant__ FrameArgs f, const __grid_constant__ VolumeArgs vol,
@@ -650,13 +653,17 @@ __global__ void __launch_bounds__(kListThreads)
 __global__ void clear_used_kernel(const __grid_constant__ VolumeArgs vol) {
   const unsigned int c = *reinterpret_cast<volatile unsigned int*>(&vol.hdr->count);
   const unsigned int n = c < vol.pool ? c : vol.pool;
-  const size_t quads = static_cast<size_t>(n) * (kBlockVoxels / 4);
+  // one 16-byte store per thread and step, consecutive threads on
+  // consecutive addresses: the records first, then the blue sums
+  const size_t records = static_cast<size_t>(n) * kBlockVoxels;
+  const size_t quads = records + records / 4;
   const float4 z = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < quads;
        i += static_cast<size_t>(gridDim.x) * blockDim.x) {
-#pragma unroll
-    for (int j = 0; j < 4; ++j) vol.twrg[4 * i + j] = z;
-    reinterpret_cast<float4*>(vol.blue)[i] = z;
+    if (i < records)
+      vol.twrg[i] = z;
+    else
+      reinterpret_cast<float4*>(vol.blue)[i - records] = z;
   }
 }
 
@@ -741,12 +748,18 @@ __global__ void weight_sum_kernel(const __grid_constant__ VolumeArgs vol,
 // around its 0-7 diagonal; a corner is inside when its mean tsdf is < 0; each
 // tetrahedron edge with ends on both sides holds a vertex at the linear zero
 // crossing, measured from its lower corner; triangles are wound with normals
-// towards positive values. One CTA of 512 threads per block: the block's
-// means and the faces of its 7 upper neighbours (looked up in the table) are
-// staged as a 9x9x9 tile in shared memory, NaN where unobserved; each thread
-// takes one cube, counts its triangles, the warp reserves space with one
-// atomicAdd, and the thread writes them.
-constexpr int kExtractThreads = 512;
+// towards positive values.
+//
+// One WARP per allocated block, with no CTA-wide barrier: lanes 0-7 look up
+// the block's 7 upper neighbours, the warp stages the 9x9x9 tile of means in
+// its own shared memory (NaN where unobserved), each lane takes 16 of the
+// 512 cubes, the warp reserves its output with one atomicAdd, and the
+// triangles go through a per-warp shared staging area so that they leave in
+// coalesced stores. Many warps per SM, each on its own block, hide the
+// latency of the lookups and loads.
+constexpr int kExtractWarps = 4;     // warps (blocks in flight) per CTA
+constexpr int kExtractStage = 64;    // triangles per output window of a warp
+constexpr int kTileVals = 9 * 9 * 9;
 
 // Tetrahedra of a cube, positively oriented; corner c = g + (c&1, c>>1&1, c>>2&1).
 __constant__ unsigned char c_tets[6][4] = {{0, 1, 3, 7}, {0, 1, 7, 5}, {0, 2, 7, 3},
@@ -760,89 +773,209 @@ __constant__ unsigned char c_pair[16][4] = {
     {1, 2, 0, 3}, {0, 0, 0, 0}, {0, 0, 0, 0}, {0, 3, 1, 2}, {1, 3, 2, 0}, {0, 0, 0, 0},
     {2, 3, 0, 1}, {0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}};
 
-struct CubeCorners {
-  float val[8];
+// Offset of cube corner c in the staged 9x9x9 tile.
+__device__ __forceinline__ int corner_offset(int c) {
+  return (c & 1) + ((c >> 1) & 1) * 9 + ((c >> 2) & 1) * 81;
+}
+
+// The 4-bit inside mask of tetrahedron t from the cube's 8-bit inside mask.
+__device__ __forceinline__ unsigned tet_bits(unsigned inside, int t) {
+  unsigned m = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) m |= ((inside >> c_tets[t][k]) & 1u) << k;
+  return m;
+}
+
+// Triangles of a cube with inside mask `inside` (0..12).
+__device__ __forceinline__ int cube_triangle_count(unsigned inside) {
+  int n = 0;
+#pragma unroll
+  for (int t = 0; t < 6; ++t) {
+    const int k = __popc(tet_bits(inside, t));
+    n += (k == 0 || k == 4) ? 0 : (k == 2 ? 2 : 1);
+  }
+  return n;
+}
+
+// A cube of the staged tile: its base voxel, the tile position of corner 0,
+// and its 8-bit inside mask (0 when a corner is unobserved or none differs).
+struct Cube {
   int gx, gy, gz;
-  float v;
+  int at;
+  unsigned inside;
 };
 
-// Vertex on the edge between cube corners a and b (either order).
-__device__ __forceinline__ void edge_vertex(const CubeCorners& C, int a, int b, float* out) {
+__device__ __forceinline__ Cube load_cube(const float* val, int c, int bx, int by, int bz) {
+  Cube C;
+  const int lx = c & 7, ly = (c >> 3) & 7, lz = c >> 6;
+  C.gx = bx * kBlockEdge + lx;
+  C.gy = by * kBlockEdge + ly;
+  C.gz = bz * kBlockEdge + lz;
+  C.at = lz * 81 + ly * 9 + lx;
+  bool ok = true;
+  unsigned inside = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const float x = val[C.at + corner_offset(k)];
+    ok = ok && !isnan(x);
+    inside |= (x < 0.0f) ? (1u << k) : 0u;
+  }
+  C.inside = (ok && inside != 0xFFu) ? inside : 0u;
+  return C;
+}
+
+// The k-th triangle (in tetrahedron order) of a cube with inside mask
+// `inside`: its name tag 2*tetrahedron + sub and its three edges as corner
+// pairs, wound with the normal towards positive values.
+__device__ __forceinline__ void cube_triangle(unsigned inside, int k, int& tag, int e[6]) {
+  int t = 0;
+  unsigned m = 0;
+  int n_in = 0;
+  for (; t < 6; ++t) {
+    m = tet_bits(inside, t);
+    n_in = __popc(m);
+    const int c = (n_in == 0 || n_in == 4) ? 0 : (n_in == 2 ? 2 : 1);
+    if (k < c) break;
+    k -= c;
+  }
+  if (t == 6) t = 5;  // unreachable: k is below the cube's count
+  const unsigned char* T = c_tets[t];
+  if (n_in == 2) {
+    const unsigned char* o = c_pair[m];
+    const int a = T[o[0]], b = T[o[1]], c = T[o[2]], d = T[o[3]];
+    // two inside (a, b), two outside (c, d): the quad a-c, a-d, b-d, b-c
+    const int q0[6] = {a, c, a, d, b, d}, q1[6] = {a, c, b, d, b, c};
+#pragma unroll
+    for (int i = 0; i < 6; ++i) e[i] = k == 0 ? q0[i] : q1[i];
+    tag = 2 * t + k;
+  } else {
+    const unsigned lone = n_in == 1 ? m : (~m & 15u);
+    const unsigned char* o = c_lone[__ffs(lone) - 1];
+    const int a = T[o[0]], b = T[o[1]], c = T[o[2]], d = T[o[3]];
+    // a lone inside corner: normal away from it; a lone outside corner: towards it
+    e[0] = a;
+    e[1] = b;
+    e[2] = a;
+    e[3] = n_in == 1 ? c : d;
+    e[4] = a;
+    e[5] = n_in == 1 ? d : c;
+    tag = 2 * t;
+  }
+}
+
+// Vertex on the edge between corners a and b of cube `cube` of the staged
+// tile, measured from the lower corner (the one whose offset bits are a
+// subset of the other's).
+__device__ __forceinline__ void tile_edge_vertex(const float* val, int cube, int bx, int by,
+                                                 int bz, float v, int a, int b, float* out) {
   const int lo = ((a & b) == a) ? a : b;
   const int hi = lo ^ a ^ b;
-  const float t = __fdiv_rn(C.val[lo], __fsub_rn(C.val[lo], C.val[hi]));
-  const int g[3] = {C.gx, C.gy, C.gz};
+  const int lx = cube & 7, ly = (cube >> 3) & 7, lz = cube >> 6;
+  const int at = lz * 81 + ly * 9 + lx;
+  const float vlo = val[at + corner_offset(lo)];
+  const float vhi = val[at + corner_offset(hi)];
+  const float t = __fdiv_rn(vlo, __fsub_rn(vlo, vhi));
+  const int g[3] = {bx * kBlockEdge + lx, by * kBlockEdge + ly, bz * kBlockEdge + lz};
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    const float plo = __fmul_rn(__fadd_rn(static_cast<float>(g[k] + ((lo >> k) & 1)), 0.5f), C.v);
-    const float phi = __fmul_rn(__fadd_rn(static_cast<float>(g[k] + ((hi >> k) & 1)), 0.5f), C.v);
+    const float plo = __fmul_rn(__fadd_rn(static_cast<float>(g[k] + ((lo >> k) & 1)), 0.5f), v);
+    const float phi = __fmul_rn(__fadd_rn(static_cast<float>(g[k] + ((hi >> k) & 1)), 0.5f), v);
     out[k] = __fadd_rn(plo, __fmul_rn(t, __fsub_rn(phi, plo)));
   }
 }
 
-__device__ __forceinline__ void write_triangle(const CubeCorners& C, int e0a, int e0b, int e1a,
-                                               int e1b, int e2a, int e2b, int tag,
-                                               unsigned pos, unsigned capacity, float* tris,
-                                               int32_t* cells) {
-  if (pos >= capacity) return;
-  if (tris) {
-    float* o = tris + 9 * static_cast<size_t>(pos);
-    edge_vertex(C, e0a, e0b, o);
-    edge_vertex(C, e1a, e1b, o + 3);
-    edge_vertex(C, e2a, e2b, o + 6);
-  }
-  if (cells) {
-    int32_t* c = cells + 4 * static_cast<size_t>(pos);
-    c[0] = C.gx;
-    c[1] = C.gy;
-    c[2] = C.gz;
-    c[3] = tag;
-  }
+constexpr int kHalo = kTileVals - kBlockVoxels;  // 217 tile points in the 7 upper neighbours
+
+__device__ __forceinline__ float mean_or_nan(float2 s) {
+  return s.y > 0.0f ? __fdiv_rn(s.x, s.y) : __int_as_float(0x7fc00000);  // NaN: unobserved
 }
 
-__device__ __forceinline__ int tet_mask(const CubeCorners& C, int t) {
-  int m = 0;
+// Stage the 9x9x9 tile of means of a block: its own 512 voxels (contiguous
+// records, coalesced loads) and the 217 voxels of the faces, edges and corner
+// of its upper neighbours (listed in `halo` as tile position << 12 |
+// neighbour << 9 | local index). Loads are issued in batches of 8 before any
+// is used, so a warp waits for three round trips.
+__device__ __forceinline__ void stage_tile(const VolumeArgs& vol, const int* nb,
+                                           const unsigned* halo, float* val, unsigned lane) {
+  const float4* own = vol.twrg + static_cast<size_t>(nb[0]) * kBlockVoxels;
 #pragma unroll
-  for (int k = 0; k < 4; ++k) m |= (C.val[c_tets[t][k]] < 0.0f) ? (1 << k) : 0;
-  return m;
+  for (int b0 = 0; b0 < kBlockVoxels / 32; b0 += 8) {
+    float2 sum[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      sum[j] = __ldg(reinterpret_cast<const float2*>(own + lane + 32 * (b0 + j)));
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int l = static_cast<int>(lane) + 32 * (b0 + j);
+      val[(l >> 6) * 81 + ((l >> 3) & 7) * 9 + (l & 7)] = mean_or_nan(sum[j]);
+    }
+  }
+  constexpr int kPer = (kHalo + 31) / 32;  // 7
+  float2 sum[kPer];
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    const int h = static_cast<int>(lane) + 32 * j;
+    sum[j] = make_float2(0.0f, 0.0f);
+    if (h < kHalo) {
+      const unsigned e = halo[h];
+      const int idx = nb[(e >> 9) & 7u];
+      if (idx >= 0)
+        sum[j] = __ldg(reinterpret_cast<const float2*>(
+            vol.twrg + static_cast<size_t>(idx) * kBlockVoxels + (e & 511u)));
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    const int h = static_cast<int>(lane) + 32 * j;
+    if (h < kHalo) val[halo[h] >> 12] = mean_or_nan(sum[j]);
+  }
 }
 
-__global__ void __launch_bounds__(kExtractThreads)
+__global__ void __launch_bounds__(32 * kExtractWarps, 8)
     extract_kernel(const __grid_constant__ VolumeArgs vol, float v, float* __restrict__ tris,
                    int32_t* __restrict__ cells, unsigned int capacity,
                    unsigned int* __restrict__ counter) {
-  __shared__ float s_val[9 * 9 * 9];
-  __shared__ int s_nb[8];
-  __shared__ int s_b[3];
-  __shared__ int s_skip;
+  __shared__ float s_val[kExtractWarps][kTileVals];
+  __shared__ int s_nb[kExtractWarps][8];
+  __shared__ float s_stage[kExtractWarps][9 * kExtractStage];
+  __shared__ unsigned s_busy[kExtractWarps][kBlockVoxels];
+  __shared__ unsigned short s_before[kExtractWarps][kBlockVoxels];
+  __shared__ unsigned s_halo[kHalo];
+  // the halo points of a tile, in tile order
+  if (threadIdx.x == 0) {
+    int h = 0;
+    for (int i = 0; i < kTileVals; ++i) {
+      const int x = i % 9, y = (i / 9) % 9, z = i / 81;
+      const int d = (x >> 3) | ((y >> 3) << 1) | ((z >> 3) << 2);
+      if (d)
+        s_halo[h++] = (static_cast<unsigned>(i) << 12) | (static_cast<unsigned>(d) << 9) |
+                      static_cast<unsigned>(local_index(x & 7, y & 7, z & 7));
+    }
+  }
+  __syncthreads();
+  const unsigned lane = threadIdx.x & 31u;
+  const int warp = threadIdx.x >> 5;
+  float* val = s_val[warp];
+  int* nb = s_nb[warp];
+  float* stage = s_stage[warp];
+  unsigned* busy = s_busy[warp];
+  unsigned short* before = s_before[warp];
   const unsigned int c = *reinterpret_cast<volatile unsigned int*>(&vol.hdr->count);
   const unsigned int units = vol.slot_index ? vol.slots : (c < vol.pool ? c : vol.pool);
-  const unsigned lane = threadIdx.x & 31u;
-  for (unsigned int unit = blockIdx.x; unit < units; unit += gridDim.x) {
-    if (threadIdx.x == 0) {
-      int bx = 0, by = 0, bz = 0, skip = 0;
-      if (vol.slot_index) {
-        const unsigned long long key = vol.table[unit].key;
-        skip = key == kEmptyKey;
-        if (!skip) unpack_key(key, bx, by, bz);
-      } else {
-        bx = vol.coords[3 * static_cast<size_t>(unit)];
-        by = vol.coords[3 * static_cast<size_t>(unit) + 1];
-        bz = vol.coords[3 * static_cast<size_t>(unit) + 2];
-      }
-      s_skip = skip;
-      s_b[0] = bx;
-      s_b[1] = by;
-      s_b[2] = bz;
+  for (unsigned int unit = blockIdx.x * kExtractWarps + warp; unit < units;
+       unit += gridDim.x * kExtractWarps) {
+    int bx = 0, by = 0, bz = 0;
+    if (vol.slot_index) {
+      const unsigned long long key = vol.table[unit].key;   // same address in every lane
+      if (key == kEmptyKey) continue;                        // uniform across the warp
+      unpack_key(key, bx, by, bz);
+    } else {
+      bx = vol.coords[3 * static_cast<size_t>(unit)];
+      by = vol.coords[3 * static_cast<size_t>(unit) + 1];
+      bz = vol.coords[3 * static_cast<size_t>(unit) + 2];
     }
-    __syncthreads();
-    if (s_skip) {  // uniform across the CTA
-      __syncthreads();
-      continue;
-    }
-    const int bx = s_b[0], by = s_b[1], bz = s_b[2];
-    if (threadIdx.x < 8) {
-      const int d = threadIdx.x;
+    if (lane < 8) {
+      const int d = static_cast<int>(lane);
       int idx = static_cast<int>(unit);
       if (d) {
         const int nx = bx + (d & 1), ny = by + ((d >> 1) & 1), nz = bz + ((d >> 2) & 1);
@@ -850,81 +983,78 @@ __global__ void __launch_bounds__(kExtractThreads)
         const bool in_range = nx < kKeyBias && ny < kKeyBias && nz < kKeyBias;
         idx = in_range ? lookup_block(vol, pack_key(nx, ny, nz), nx, ny, nz) : kAbsent;
       }
-      s_nb[d] = idx >= 0 ? idx : -1;
+      nb[d] = idx >= 0 ? idx : -1;
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < 9 * 9 * 9; i += kExtractThreads) {
-      const int x = i % 9, y = (i / 9) % 9, z = i / 81;
-      const int idx = s_nb[(x >> 3) | ((y >> 3) << 1) | ((z >> 3) << 2)];
-      float m = __int_as_float(0x7fc00000);  // NaN: unobserved
-      if (idx >= 0) {
-        const float4 sum = vol.twrg[static_cast<size_t>(idx) * kBlockVoxels +
-                                    local_index(x & 7, y & 7, z & 7)];
-        if (sum.y > 0.0f) m = __fdiv_rn(sum.x, sum.y);
+    __syncwarp();
+    stage_tile(vol, nb, s_halo, val, lane);
+    __syncwarp();
+    // the cubes that make triangles, listed warp-wide with their inside
+    // masks (cube | mask << 9) and the running count of triangles before each
+    unsigned nbusy = 0;
+    int total = 0;
+    for (int j = 0; j < kBlockVoxels / 32; ++j) {
+      const int cube = static_cast<int>(lane) + 32 * j;
+      const Cube C = load_cube(val, cube, bx, by, bz);
+      const int cnt = C.inside ? cube_triangle_count(C.inside) : 0;
+      const unsigned m = __ballot_sync(0xffffffffu, cnt > 0);
+      int incl = cnt;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (static_cast<int>(lane) >= o) incl += y;
       }
-      s_val[i] = m;
-    }
-    __syncthreads();
-
-    CubeCorners C;
-    const int lx = threadIdx.x & 7, ly = (threadIdx.x >> 3) & 7, lz = threadIdx.x >> 6;
-    C.gx = bx * kBlockEdge + lx;
-    C.gy = by * kBlockEdge + ly;
-    C.gz = bz * kBlockEdge + lz;
-    C.v = v;
-    bool ok = true;
-    unsigned inside = 0;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      C.val[k] = s_val[(lz + (k >> 2)) * 81 + (ly + ((k >> 1) & 1)) * 9 + lx + (k & 1)];
-      ok = ok && !isnan(C.val[k]);
-      inside |= (C.val[k] < 0.0f) ? (1u << k) : 0u;
-    }
-    int ntri = 0;
-    if (ok && inside != 0u && inside != 0xFFu) {
-#pragma unroll
-      for (int t = 0; t < 6; ++t) {
-        const int n_in = __popc(tet_mask(C, t));
-        ntri += (n_in == 0 || n_in == 4) ? 0 : (n_in == 2 ? 2 : 1);
+      if (cnt > 0) {
+        const unsigned at = nbusy + __popc(m & ((1u << lane) - 1u));
+        busy[at] = static_cast<unsigned>(cube) | (C.inside << 9);
+        before[at] = static_cast<unsigned short>(total + incl - cnt);
       }
+      nbusy += __popc(m);
+      total += __shfl_sync(0xffffffffu, incl, 31);
     }
-    // warp-wide exclusive scan of the counts, one reservation per warp
-    int incl = ntri;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, incl, o);
-      if (static_cast<int>(lane) >= o) incl += y;
-    }
-    const int total = __shfl_sync(0xffffffffu, incl, 31);
     unsigned base = 0;
-    if (lane == 31 && total) base = atomicAdd(counter, static_cast<unsigned>(total));
-    base = __shfl_sync(0xffffffffu, base, 31);
-    unsigned pos = base + static_cast<unsigned>(incl - ntri);
-    if (ntri) {
-#pragma unroll 1
-      for (int t = 0; t < 6; ++t) {
-        const int m = tet_mask(C, t);
-        const int n_in = __popc(m);
-        if (n_in == 0 || n_in == 4) continue;
-        const unsigned char* T = c_tets[t];
-        if (n_in == 2) {
-          const unsigned char* o = c_pair[m];
-          const int a = T[o[0]], b = T[o[1]], cc = T[o[2]], d = T[o[3]];
-          write_triangle(C, a, cc, a, d, b, d, 2 * t, pos++, capacity, tris, cells);
-          write_triangle(C, a, cc, b, d, b, cc, 2 * t + 1, pos++, capacity, tris, cells);
-        } else {
-          const int lone = n_in == 1 ? m : (~m & 15);
-          const int i = __ffs(lone) - 1;
-          const unsigned char* o = c_lone[i];
-          const int a = T[o[0]], b = T[o[1]], cc = T[o[2]], d = T[o[3]];
-          if (n_in == 1)
-            write_triangle(C, a, b, a, cc, a, d, 2 * t, pos++, capacity, tris, cells);
-          else
-            write_triangle(C, a, b, a, d, a, cc, 2 * t, pos++, capacity, tris, cells);
+    if (lane == 0 && total) base = atomicAdd(counter, static_cast<unsigned>(total));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    __syncwarp();
+    if (total && (tris || cells)) {
+      // one triangle per lane: find its cube by binary search over the
+      // running counts, then its tetrahedron; windows of kExtractStage
+      // triangles are staged and stored in coalesced words
+      for (unsigned w0 = 0; w0 < static_cast<unsigned>(total); w0 += kExtractStage) {
+        const unsigned n = min(static_cast<unsigned>(kExtractStage), total - w0);
+        for (unsigned q = lane; q < n; q += 32) {
+          const unsigned tri = w0 + q;
+          unsigned lo = 0, hi = nbusy;  // last entry with before <= tri
+          while (hi - lo > 1) {
+            const unsigned mid = (lo + hi) >> 1;
+            if (before[mid] <= tri) lo = mid; else hi = mid;
+          }
+          const unsigned e0 = busy[lo];
+          const int cube = static_cast<int>(e0 & 511u);
+          int tag, e[6];
+          cube_triangle(e0 >> 9, static_cast<int>(tri - before[lo]), tag, e);
+          const unsigned pos = base + tri;
+          if (tris) {
+            float* o = stage + 9 * q;
+            tile_edge_vertex(val, cube, bx, by, bz, v, e[0], e[1], o);
+            tile_edge_vertex(val, cube, bx, by, bz, v, e[2], e[3], o + 3);
+            tile_edge_vertex(val, cube, bx, by, bz, v, e[4], e[5], o + 6);
+          }
+          if (cells && pos < capacity)
+            reinterpret_cast<int4*>(cells)[pos] =
+                make_int4(bx * kBlockEdge + (cube & 7), by * kBlockEdge + ((cube >> 3) & 7),
+                          bz * kBlockEdge + (cube >> 6), tag);
         }
+        __syncwarp();
+        if (tris) {
+          const size_t o0 = 9 * (static_cast<size_t>(base) + w0);
+          const size_t ocap = 9 * static_cast<size_t>(capacity);
+          for (unsigned w = lane; w < 9 * n; w += 32)
+            if (o0 + w < ocap) tris[o0 + w] = stage[w];
+        }
+        __syncwarp();
       }
     }
-    __syncthreads();  // the tile is rewritten for the next block
+    __syncwarp();  // the tile, neighbour list and staging are reused
   }
 }
 
@@ -1386,20 +1516,21 @@ cudaError_t launch_integrate(const FrameArgs& f, const VolumeArgs& vol, int mode
 
 template <int P, int M>
 static cudaError_t launch_tile_fused_kernel(const FrameArgs& f, const VolumeArgs& vol,
-                                            cudaStream_t s) {
+                                            int mode, cudaStream_t s) {
+  (void)mode;
   const int tx = tiles_of(f.W);
   tile_fused_kernel<P, M><<<tx * tiles_of(f.H), kThreads, 0, s>>>(f, vol, tx);
   return cudaGetLastError();
 }
 
 template <int P>
-static cudaError_t launch_tile_fused_m(const FrameArgs& f, const VolumeArgs& vol,
+static cudaError_t launch_tile_fused_m(const FrameArgs& f, const VolumeArgs& vol, int mode,
                                        cudaStream_t s) {
   switch (f.M) {
-    case 2: return launch_tile_fused_kernel<P, 2>(f, vol, s);
-    case 4: return launch_tile_fused_kernel<P, 4>(f, vol, s);
-    case 8: return launch_tile_fused_kernel<P, 8>(f, vol, s);
-    default: return launch_tile_fused_kernel<P, 0>(f, vol, s);
+    case 2: return launch_tile_fused_kernel<P, 2>(f, vol, mode, s);
+    case 4: return launch_tile_fused_kernel<P, 4>(f, vol, mode, s);
+    case 8: return launch_tile_fused_kernel<P, 8>(f, vol, mode, s);
+    default: return launch_tile_fused_kernel<P, 0>(f, vol, mode, s);
   }
 }
 
@@ -1408,9 +1539,9 @@ cudaError_t launch_fused(const FrameArgs& f, const VolumeArgs& vol, int probe_lo
   cudaError_t e;
   if (mode == 2) {
     switch (probe_load) {
-      case kLoadL2: e = launch_tile_fused_m<kLoadL2>(f, vol, s); break;
-      case kLoadRelaxed: e = launch_tile_fused_m<kLoadRelaxed>(f, vol, s); break;
-      default: e = launch_tile_fused_m<kLoadCached>(f, vol, s); break;
+      case kLoadL2: e = launch_tile_fused_m<kLoadL2>(f, vol, mode, s); break;
+      case kLoadRelaxed: e = launch_tile_fused_m<kLoadRelaxed>(f, vol, mode, s); break;
+      default: e = launch_tile_fused_m<kLoadCached>(f, vol, mode, s); break;
     }
   } else {
     e = launch_warp_p<kOpFused>(f, vol, probe_load, s);
@@ -1539,9 +1670,9 @@ cudaError_t launch_clear_used(const VolumeArgs& vol, int sm_count, cudaStream_t 
 cudaError_t launch_extract(const VolumeArgs& vol, float v, float* tris, int32_t* cells,
                            unsigned int capacity, unsigned int* counter, int sm_count,
                            cudaStream_t s) {
-  // persistent: a few CTAs of 512 threads per SM loop over the blocks
-  extract_kernel<<<sm_count * 4, kExtractThreads, 0, s>>>(vol, v, tris, cells, capacity,
-                                                         counter);
+  // persistent: every warp loops over blocks; 8 CTAs of 4 warps per SM
+  extract_kernel<<<sm_count * 8, 32 * kExtractWarps, 0, s>>>(vol, v, tris, cells, capacity,
+                                                            counter);
   note_launch();
   return cudaGetLastError();
 }
