@@ -555,7 +555,7 @@ def run_serving(args, torch, serving, bank):
     """Config-5 style: 256 sessions, Poisson arrivals at 30 fps each, 10 s
     window, volumes admitted by memory; continuous batching against per-frame
     launches on the same schedule, at the nominal rate and with arrivals
-    compressed args.serve_stress times. Latency = completion - arrival."""
+    compressed by each factor in args.serve_stress. Latency = completion - arrival."""
     free, _ = torch.cuda.mem_get_info()
     budget = min(0.7 * free, 200e9)
     plans = serving.plan_sessions(args.serve_sessions, window=args.serve_window,
@@ -568,7 +568,7 @@ def run_serving(args, torch, serving, bank):
            "admission_wait_ms_p99": round(float(np.percentile(waits, 99)) * 1e3, 2),
            "frames_offered": int(sum(len(p.arrivals) for p in admitted))}
     out["server"] = "tsdf_server (native continuous batching) vs one launch per frame"
-    for speed in (1.0, args.serve_stress):
+    for speed in [1.0] + [float(x) for x in str(args.serve_stress).split(",") if x]:
         into = out if speed == 1.0 else out.setdefault(f"stress_{speed:g}x", {})
         for name, mode in (("batched", 0), ("per_frame", 1)):
             res, st, _ = serving.native_replay(torch, bank, plans, mode, speed=speed)
@@ -773,8 +773,8 @@ def main():
                     help="nvidia-smi sampling interval during the timed region")
     ap.add_argument("--serve-sessions", type=int, default=256)
     ap.add_argument("--serve-window", type=float, default=10.0)
-    ap.add_argument("--serve-stress", type=float, default=3.0,
-                    help="arrival-rate multiple of the second serving run")
+    ap.add_argument("--serve-stress", default="3,10",
+                    help="arrival-rate multiples of the further serving runs (comma-separated)")
     ap.add_argument("--bank-frames", type=int, default=24)
     ap.add_argument("--sweep-frames", type=int, default=142,
                     help="orbit frames rendered for the load-factor sweep (0 = no sweep)")

@@ -200,9 +200,10 @@ struct PointKeys {
 
 enum TileOp { kOpAllocate = 0, kOpIntegrate = 1, kOpFused = 2 };
 
-// Resolve one key on its own (paths that could not use the tile list).
+// Resolve one key on its own (paths that could not use the tile list: rare,
+// so kept out of line to keep the kernels' hot code small).
 template <int Op, int P>
-__device__ __forceinline__ int resolve_single(const VolumeArgs& vol, unsigned long long key) {
+__device__ __noinline__ int resolve_single(const VolumeArgs& vol, unsigned long long key) {
   int bx, by, bz;
   unpack_key(key, bx, by, bz);
   if (Op == kOpAllocate) return insert_block<P, false>(vol, key, bx, by, bz);
@@ -343,7 +344,7 @@ __device__ __forceinline__ void tile_allocate_body(TileShared& T, const FrameArg
 }
 
 template <int P, int M>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 4)
     tile_allocate_kernel(const __grid_constant__ FrameArgs f,
                          const __grid_constant__ VolumeArgs vol, int tiles_x) {
   __shared__ TileShared T;
