@@ -35,7 +35,11 @@
 //   R5 single-precision decision arithmetic with a fixed operation order and
 //      explicit fused multiply-adds (fmaf), so that every integer the geometry
 //      decides (voxel index, pixel index, accept/reject) is reproducible
-//      bit-for-bit by any IEEE-754 implementation of the same steps.
+//      bit-for-bit by any IEEE-754 implementation of the same steps. The ray
+//      is taken to the world frame once per point (P = R p + t, D = R d) and
+//      sample k is P + t_k D; the voxel centre reaches the camera frame by one
+//      per-frame affine map of the integer voxel, c = A g + b with A = v R^T
+//      and b = R^T (v/2 - t).
 //   R6 block coordinates must fit the 21-bit biased key (|b| < 2^20); voxels
 //      outside are rejected and counted.
 // Sums of tsdf and colour are accumulated in double (the reference value);
@@ -156,6 +160,16 @@ int oracle_fuse(void* h, const float* depth, int W, int H, const float* intr,
     for (int j = 0; j < 3; ++j) R[i][j] = pose[4 * i + j];
     t[i] = pose[4 * i + 3];
   }
+  // R5: the voxel centre in the camera frame, R^T ((g + 1/2) v - t), as one
+  // affine map of the integer voxel g: c = A g + b, A = v R^T,
+  // b = R^T (v/2 - t), each constant computed once per frame.
+  float A[3][3], bc[3], half_minus_t[3];
+  for (int i = 0; i < 3; ++i) half_minus_t[i] = std::fmaf(0.5f, v, -t[i]);
+  for (int j = 0; j < 3; ++j) {
+    for (int i = 0; i < 3; ++i) A[j][i] = v * R[i][j];
+    bc[j] = std::fmaf(R[2][j], half_minus_t[2],
+                      std::fmaf(R[1][j], half_minus_t[1], R[0][j] * half_minus_t[0]));
+  }
 
   // Per-frame bookkeeping for the statistics.
   std::map<Coord, std::array<uint8_t, kVox>> touched;
@@ -169,12 +183,18 @@ int oracle_fuse(void* h, const float* depth, int W, int H, const float* intr,
       if (!std::isfinite(d) || !(d > 0.0f)) continue;
       st[0]++;
 
-      // Back-projection and unit view ray (camera frame).
+      // Back-projection and unit view ray (camera frame), then both in the
+      // world frame once per point (R5): P = R p + t, D = R d.
       const float rx = (static_cast<float>(pu) - cx) / fx;
       const float ry = (static_cast<float>(pv) - cy) / fy;
       const float pcx = rx * d, pcy = ry * d, pcz = d;
       const float n = std::sqrt(std::fmaf(rx, rx, std::fmaf(ry, ry, 1.0f)));
       const float dx = rx / n, dy = ry / n, dz = 1.0f / n;
+      float Pw[3], Dw[3];
+      for (int i = 0; i < 3; ++i) {
+        Pw[i] = std::fmaf(R[i][2], pcz, std::fmaf(R[i][1], pcy, std::fmaf(R[i][0], pcx, t[i])));
+        Dw[i] = std::fmaf(R[i][2], dz, std::fmaf(R[i][1], dy, R[i][0] * dx));
+      }
 
       float col[3] = {0.0f, 0.0f, 0.0f};
       if (rgb) {
@@ -189,13 +209,10 @@ int oracle_fuse(void* h, const float* depth, int W, int H, const float* intr,
       for (int k = 0; k <= 2 * M; ++k) {
         st[1]++;
         const float tk = static_cast<float>(k - M) * v;
-        const float sc[3] = {std::fmaf(tk, dx, pcx), std::fmaf(tk, dy, pcy),
-                             std::fmaf(tk, dz, pcz)};
         int32_t g[3];
         bool in_range = true;
         for (int i = 0; i < 3; ++i) {
-          const float sw =
-              std::fmaf(R[i][2], sc[2], std::fmaf(R[i][1], sc[1], std::fmaf(R[i][0], sc[0], t[i])));
+          const float sw = std::fmaf(tk, Dw[i], Pw[i]);  // the sample, world frame
           const float fg = std::floor(sw * inv_v);
           // R6: block coordinate must lie in [-2^20, 2^20), voxel in [-2^23, 2^23)
           if (!(fg >= -8388608.0f && fg < 8388608.0f)) {
@@ -216,15 +233,12 @@ int oracle_fuse(void* h, const float* depth, int W, int H, const float* intr,
         if (seen) continue;
         walk.push_back({g[0], g[1], g[2]});
 
-        // Voxel centre, world then camera frame.
-        float e[3];
-        for (int i = 0; i < 3; ++i) {
-          const float cw = (static_cast<float>(g[i]) + 0.5f) * v;
-          e[i] = cw - t[i];
-        }
+        // Voxel centre in the camera frame: c = A g + b.
         float cc[3];
-        for (int j = 0; j < 3; ++j)  // R^T e, column j of R
-          cc[j] = std::fmaf(R[2][j], e[2], std::fmaf(R[1][j], e[1], R[0][j] * e[0]));
+        for (int j = 0; j < 3; ++j)
+          cc[j] = std::fmaf(A[j][2], static_cast<float>(g[2]),
+                            std::fmaf(A[j][1], static_cast<float>(g[1]),
+                                      std::fmaf(A[j][0], static_cast<float>(g[0]), bc[j])));
 
         // Occlusion test (R3).
         if (!(cc[2] > 0.0f)) continue;

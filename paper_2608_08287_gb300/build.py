@@ -21,8 +21,11 @@ LIB = os.path.join(BUILD, "libtsdf.so")
 SOURCES = ("tsdf_api.cu", "tsdf_batch.cu", "tsdf_kernels.cu", "tsdf_noalloc.cu",
            "tsdf_serve.cu", "tsdf_tune.cu")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas",
-              "-warn-spills", "--expt-relaxed-constexpr"]
+# Host code is compiled with contraction off: the per-frame constants the
+# kernels' decisions depend on are computed in a fixed order of IEEE
+# single-precision operations.
+NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler",
+              "-ffp-contract=off", "-Xptxas", "-warn-spills", "--expt-relaxed-constexpr"]
 
 
 def nvcc_path() -> str:

@@ -162,6 +162,16 @@ tsdf_status make_frame(const tsdf_volume* v, const float* depth, int w, int h,
     for (int j = 0; j < 3; ++j) f->R[3 * i + j] = pose->m[4 * i + j];
     f->t[i] = pose->m[4 * i + 3];
   }
+  // The voxel-centre map c = A g + b, A = v R^T, b = R^T (v/2 - t), in this
+  // fixed order of single-precision operations (the library is built with
+  // contraction off, and the fused steps are explicit).
+  float half_minus_t[3];
+  for (int i = 0; i < 3; ++i) half_minus_t[i] = std::fmaf(0.5f, v->voxel, -f->t[i]);
+  for (int j = 0; j < 3; ++j) {
+    for (int i = 0; i < 3; ++i) f->A[3 * j + i] = v->voxel * f->R[3 * i + j];
+    f->b[j] = std::fmaf(f->R[6 + j], half_minus_t[2],
+                        std::fmaf(f->R[3 + j], half_minus_t[1], f->R[j] * half_minus_t[0]));
+  }
   f->v = v->voxel;
   f->inv_v = 1.0f / v->voxel;
   f->tau = v->trunc;

@@ -71,6 +71,11 @@ struct FrameArgs {
   float fx, fy, cx, cy;
   float R[9];              // camera-to-world rotation, row-major
   float t[3];              // camera-to-world translation
+  // Voxel centre to camera frame as one affine map of the integer voxel g:
+  // c = A g + b with A = v R^T (row j: v * column j of R) and
+  // b = R^T (v/2 - t), so that c = R^T ((g + 1/2) v - t).
+  float A[9];
+  float b[3];
   float v, inv_v;          // voxel size and its IEEE reciprocal
   float tau, neg_tau, inv_tau;
   int M;                   // half band, samples k = 0..2M
@@ -132,8 +137,8 @@ struct __align__(16) BatchHeader {
 // ----------------------------------------------------------------------------
 struct Ray {
   float d;                 // the point's depth
-  float px, py, pz;        // back-projected point, camera frame
-  float dx, dy, dz;        // unit view ray, camera frame
+  float px, py, pz;        // back-projected point, world frame
+  float dx, dy, dz;        // unit view ray, world frame
 };
 
 // Back-project pixel (u, v) and build its unit view ray. False if the depth
@@ -143,13 +148,17 @@ __device__ __forceinline__ bool make_ray(const FrameArgs& f, int u, int v, float
   const float rx = __fdiv_rn(__fsub_rn(static_cast<float>(u), f.cx), f.fx);
   const float ry = __fdiv_rn(__fsub_rn(static_cast<float>(v), f.cy), f.fy);
   r.d = d;
-  r.px = __fmul_rn(rx, d);
-  r.py = __fmul_rn(ry, d);
-  r.pz = d;
+  // camera frame: the point and the unit ray
+  const float cpx = __fmul_rn(rx, d), cpy = __fmul_rn(ry, d), cpz = d;
   const float n = __fsqrt_rn(__fmaf_rn(rx, rx, __fmaf_rn(ry, ry, 1.0f)));
-  r.dx = __fdiv_rn(rx, n);
-  r.dy = __fdiv_rn(ry, n);
-  r.dz = __fdiv_rn(1.0f, n);
+  const float cdx = __fdiv_rn(rx, n), cdy = __fdiv_rn(ry, n), cdz = __fdiv_rn(1.0f, n);
+  // world frame, once per point: P = R p + t, D = R d
+  r.px = __fmaf_rn(f.R[2], cpz, __fmaf_rn(f.R[1], cpy, __fmaf_rn(f.R[0], cpx, f.t[0])));
+  r.py = __fmaf_rn(f.R[5], cpz, __fmaf_rn(f.R[4], cpy, __fmaf_rn(f.R[3], cpx, f.t[1])));
+  r.pz = __fmaf_rn(f.R[8], cpz, __fmaf_rn(f.R[7], cpy, __fmaf_rn(f.R[6], cpx, f.t[2])));
+  r.dx = __fmaf_rn(f.R[2], cdz, __fmaf_rn(f.R[1], cdy, __fmul_rn(f.R[0], cdx)));
+  r.dy = __fmaf_rn(f.R[5], cdz, __fmaf_rn(f.R[4], cdy, __fmul_rn(f.R[3], cdx)));
+  r.dz = __fmaf_rn(f.R[8], cdz, __fmaf_rn(f.R[7], cdy, __fmul_rn(f.R[6], cdx)));
   return true;
 }
 
@@ -158,12 +167,9 @@ __device__ __forceinline__ bool make_ray(const FrameArgs& f, int u, int v, float
 __device__ __forceinline__ bool sample_voxel(const FrameArgs& f, const Ray& r, int k, int& gx,
                                              int& gy, int& gz) {
   const float tk = __fmul_rn(static_cast<float>(k - f.M), f.v);
-  const float sx = __fmaf_rn(tk, r.dx, r.px);
-  const float sy = __fmaf_rn(tk, r.dy, r.py);
-  const float sz = __fmaf_rn(tk, r.dz, r.pz);
-  const float wx = __fmaf_rn(f.R[2], sz, __fmaf_rn(f.R[1], sy, __fmaf_rn(f.R[0], sx, f.t[0])));
-  const float wy = __fmaf_rn(f.R[5], sz, __fmaf_rn(f.R[4], sy, __fmaf_rn(f.R[3], sx, f.t[1])));
-  const float wz = __fmaf_rn(f.R[8], sz, __fmaf_rn(f.R[7], sy, __fmaf_rn(f.R[6], sx, f.t[2])));
+  const float wx = __fmaf_rn(tk, r.dx, r.px);
+  const float wy = __fmaf_rn(tk, r.dy, r.py);
+  const float wz = __fmaf_rn(tk, r.dz, r.pz);
   const float qx = floorf(__fmul_rn(wx, f.inv_v));
   const float qy = floorf(__fmul_rn(wy, f.inv_v));
   const float qz = floorf(__fmul_rn(wz, f.inv_v));
@@ -184,15 +190,14 @@ __device__ __forceinline__ bool sample_voxel(const FrameArgs& f, const Ray& r, i
 // voxel_accept takes the gathered d'.
 __device__ __forceinline__ int voxel_project(const FrameArgs& f, int gx, int gy, int gz,
                                              float& zc) {
-  const float ex = __fsub_rn(__fmul_rn(__fadd_rn(static_cast<float>(gx), 0.5f), f.v), f.t[0]);
-  const float ey = __fsub_rn(__fmul_rn(__fadd_rn(static_cast<float>(gy), 0.5f), f.v), f.t[1]);
-  const float ez = __fsub_rn(__fmul_rn(__fadd_rn(static_cast<float>(gz), 0.5f), f.v), f.t[2]);
-  // R^T e: column j of R is R[j], R[3+j], R[6+j]
-  const float ccz = __fmaf_rn(f.R[8], ez, __fmaf_rn(f.R[5], ey, __fmul_rn(f.R[2], ex)));
+  // c = A g + b (the per-frame affine map of the voxel centre), g exact in float
+  const float fgx = static_cast<float>(gx), fgy = static_cast<float>(gy),
+              fgz = static_cast<float>(gz);
+  const float ccz = __fmaf_rn(f.A[8], fgz, __fmaf_rn(f.A[7], fgy, __fmaf_rn(f.A[6], fgx, f.b[2])));
   zc = ccz;
   if (!(ccz > 0.0f)) return -1;
-  const float ccx = __fmaf_rn(f.R[6], ez, __fmaf_rn(f.R[3], ey, __fmul_rn(f.R[0], ex)));
-  const float ccy = __fmaf_rn(f.R[7], ez, __fmaf_rn(f.R[4], ey, __fmul_rn(f.R[1], ex)));
+  const float ccx = __fmaf_rn(f.A[2], fgz, __fmaf_rn(f.A[1], fgy, __fmaf_rn(f.A[0], fgx, f.b[0])));
+  const float ccy = __fmaf_rn(f.A[5], fgz, __fmaf_rn(f.A[4], fgy, __fmaf_rn(f.A[3], fgx, f.b[1])));
   const float iz = __frcp_rn(ccz);
   const float qu = floorf(__fadd_rn(__fmaf_rn(f.fx, __fmul_rn(ccx, iz), f.cx), 0.5f));
   const float qv = floorf(__fadd_rn(__fmaf_rn(f.fy, __fmul_rn(ccy, iz), f.cy), 0.5f));
@@ -234,12 +239,9 @@ __device__ __forceinline__ unsigned walk_point(const FrameArgs& f, const Ray& r,
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     const float tk = __fmul_rn(static_cast<float>(k - M), f.v);
-    const float sx = __fmaf_rn(tk, r.dx, r.px);
-    const float sy = __fmaf_rn(tk, r.dy, r.py);
-    const float sz = __fmaf_rn(tk, r.dz, r.pz);
-    const float wx = __fmaf_rn(f.R[2], sz, __fmaf_rn(f.R[1], sy, __fmaf_rn(f.R[0], sx, f.t[0])));
-    const float wy = __fmaf_rn(f.R[5], sz, __fmaf_rn(f.R[4], sy, __fmaf_rn(f.R[3], sx, f.t[1])));
-    const float wz = __fmaf_rn(f.R[8], sz, __fmaf_rn(f.R[7], sy, __fmaf_rn(f.R[6], sx, f.t[2])));
+    const float wx = __fmaf_rn(tk, r.dx, r.px);
+    const float wy = __fmaf_rn(tk, r.dy, r.py);
+    const float wz = __fmaf_rn(tk, r.dz, r.pz);
     const float qx = floorf(__fmul_rn(wx, f.inv_v));
     const float qy = floorf(__fmul_rn(wy, f.inv_v));
     const float qz = floorf(__fmul_rn(wz, f.inv_v));

@@ -566,7 +566,7 @@ __device__ __forceinline__ void scatter_body(const FrameArgs& f, const VolumeArg
 }
 
 template <int M>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 4)
     integrate_scatter_kernel(const __grid_constant__ FrameArgs f,
                              const __grid_constant__ VolumeArgs vol, int tiles_x) {
   scatter_body<M>(f, vol, blockIdx.x, tiles_x);

@@ -64,6 +64,10 @@ def fuse_dense(depth, intr, pose, voxel, trunc, rgb=None):
     pc = [rx * d, ry * d, d]
     n = np.sqrt(fma32(rx, rx, fma32(ry, ry, F32(1.0))))
     dr = [rx / n, ry / n, F32(1.0) / n]
+    # the ray in the world frame: start P = R p + t, direction D = R d
+    Pw = [fma32(R[i, 2], pc[2], fma32(R[i, 1], pc[1], fma32(R[i, 0], pc[0], t[i])))
+          for i in range(3)]
+    Dw = [fma32(R[i, 2], dr[2], fma32(R[i, 1], dr[1], R[i, 0] * dr[0])) for i in range(3)]
 
     K = 2 * M + 1
     npts = d.shape[0]
@@ -71,9 +75,8 @@ def fuse_dense(depth, intr, pose, voxel, trunc, rgb=None):
     ok = np.ones((K, npts), dtype=bool)
     for k in range(K):
         tk = F32(k - M) * v
-        sc = [fma32(tk, dr[i], pc[i]) for i in range(3)]
         for i in range(3):
-            sw = fma32(R[i, 2], sc[2], fma32(R[i, 1], sc[1], fma32(R[i, 0], sc[0], t[i])))
+            sw = fma32(tk, Dw[i], Pw[i])
             fg = np.floor(sw * inv_v)
             ok[k] &= (fg >= F32(-8388608.0)) & (fg < F32(8388608.0))
             G[k, :, i] = np.where(np.isfinite(fg), fg, 0).astype(np.int64)
@@ -84,10 +87,13 @@ def fuse_dense(depth, intr, pose, voxel, trunc, rgb=None):
             first[k] &= ~np.all(G[k] == G[j], axis=1)
     keep = ok & first
 
-    # voxel centre in the camera frame
+    # voxel centre in the camera frame, c = A g + b: A = v R^T, b = R^T (v/2 - t)
     gf = G.astype(F32)
-    e = [(gf[:, :, i] + F32(0.5)) * v - t[i] for i in range(3)]
-    cc = [fma32(R[2, j], e[2], fma32(R[1, j], e[1], R[0, j] * e[0])) for j in range(3)]
+    h = [fma32(F32(0.5), v, -t[i]) for i in range(3)]
+    A = [[v * R[i, j] for i in range(3)] for j in range(3)]
+    b = [fma32(R[2, j], h[2], fma32(R[1, j], h[1], R[0, j] * h[0])) for j in range(3)]
+    cc = [fma32(A[j][2], gf[:, :, 2], fma32(A[j][1], gf[:, :, 1], fma32(A[j][0], gf[:, :, 0], b[j])))
+          for j in range(3)]
     zc = cc[2]
     front = zc > F32(0.0)
     with np.errstate(divide="ignore", invalid="ignore", over="ignore"):
