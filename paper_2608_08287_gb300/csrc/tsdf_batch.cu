@@ -46,9 +46,9 @@ struct tsdf_batch {
 
 namespace {
 
-long long config_key(const tsdf_batch* b) {
-  return ((((static_cast<long long>(b->probe_load) * 4 + b->allocate_mode) * 4 +
-            b->integrate_mode) * 4 + b->fuse_mode) * 64) + b->factor;
+long long config_key(const tsdf_batch* b, bool all_m4) {
+  return (((((static_cast<long long>(b->probe_load) * 4 + b->allocate_mode) * 4 +
+             b->integrate_mode) * 4 + b->fuse_mode) * 64) + b->factor) * 2 + (all_m4 ? 1 : 0);
 }
 
 void drop_graphs(tsdf_batch* b) {
@@ -59,13 +59,14 @@ void drop_graphs(tsdf_batch* b) {
   }
 }
 
-cudaError_t enqueue(tsdf_batch* b, int slot, size_t bytes, int grid_limit, cudaStream_t s) {
+cudaError_t enqueue(tsdf_batch* b, int slot, size_t bytes, int grid_limit, bool all_m4,
+                    cudaStream_t s) {
   cudaError_t e = cudaMemcpyAsync(b->table_dev[slot], b->table_host[slot], bytes,
                                   cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return e;
   return tsdf::launch_batch(static_cast<const tsdf::BatchHeader*>(b->table_dev[slot]),
                             b->probe_load, b->allocate_mode, b->integrate_mode, b->fuse_mode,
-                            b->factor, grid_limit, s);
+                            b->factor, grid_limit, all_m4, s);
 }
 
 // A batch smaller than this many tiles is launched directly with a grid of its
@@ -180,11 +181,13 @@ tsdf_status tsdf_fuse_batch_async(tsdf_batch* b, const tsdf_frame* frames, int n
   tsdf::BatchHeader* hdr = reinterpret_cast<tsdf::BatchHeader*>(host);
   tsdf::SessionArgs* S = reinterpret_cast<tsdf::SessionArgs*>(hdr + 1);
   int tiles = 0;
+  bool all_m4 = true;
   for (int i = 0; i < n; ++i) {
     tsdf_volume* v = frames[i].volume;
     tsdf::make_frame(v, frames[i].depth, frames[i].width, frames[i].height, &frames[i].intr,
                      &frames[i].pose, frames[i].rgb, &S[i].f);
     S[i].vol = v->va;
+    all_m4 = all_m4 && S[i].f.M == 4;
     v->dirty = true;
     S[i].tiles_x = (frames[i].width + 15) / 16;
     S[i].tile_begin = tiles;
@@ -198,7 +201,7 @@ tsdf_status tsdf_fuse_batch_async(tsdf_batch* b, const tsdf_frame* frames, int n
   cudaStream_t s = as_stream(stream);
   cudaError_t e = cudaSuccess;
   if (b->use_graph && tiles >= kGraphMinTiles) {
-    const long long key = config_key(b);
+    const long long key = config_key(b, all_m4);
     if (b->exec_key[slot] != key) {
       if (b->exec[slot]) cudaGraphExecDestroy(b->exec[slot]);
       b->exec[slot] = nullptr;
@@ -206,7 +209,7 @@ tsdf_status tsdf_fuse_batch_async(tsdf_batch* b, const tsdf_frame* frames, int n
       e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal);
       if (e == cudaSuccess) {
         // the whole table capacity is copied, so the graph serves any n
-        const cudaError_t e1 = enqueue(b, slot, b->table_bytes, 0, b->capture);
+        const cudaError_t e1 = enqueue(b, slot, b->table_bytes, 0, all_m4, b->capture);
         e = cudaStreamEndCapture(b->capture, &g);
         if (e == cudaSuccess) e = e1;
       }
@@ -223,7 +226,7 @@ tsdf_status tsdf_fuse_batch_async(tsdf_batch* b, const tsdf_frame* frames, int n
   } else {
     const size_t bytes =
         sizeof(tsdf::BatchHeader) + static_cast<size_t>(n) * sizeof(tsdf::SessionArgs);
-    e = enqueue(b, slot, bytes, tiles, s);
+    e = enqueue(b, slot, bytes, tiles, all_m4, s);
   }
   if (e == cudaSuccess) e = cudaEventRecord(b->done[slot], s);
   if (e != cudaSuccess) return from_cuda(e);

@@ -1376,7 +1376,10 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
-template <int P>
+// MF: 4 when every frame of the batch has half band M = 4 (the common case:
+// the body is then compiled for that band alone, with fewer registers), else
+// 0 and each tile dispatches on its frame's band.
+template <int P, int MF>
 __global__ void __launch_bounds__(kThreads, 4)
     batch_tile_fused_kernel(const BatchHeader* __restrict__ table) {
   __shared__ FusedTileShared S;
@@ -1395,7 +1398,7 @@ __global__ void __launch_bounds__(kThreads, 4)
       cur = s;
     }
     __syncthreads();
-    if (sa.f.M == 4)
+    if (MF == 4 || sa.f.M == 4)
       tile_fused_body<P, 4>(S, sa.f, sa.vol, tile - sa.tile_begin, sa.tiles_x);
     else
       tile_fused_body<P, 0>(S, sa.f, sa.vol, tile - sa.tile_begin, sa.tiles_x);
@@ -1583,17 +1586,22 @@ static cudaError_t launch_persistent(K kernel, const BatchHeader* table, int fac
   return cudaGetLastError();
 }
 
+template <int P>
+static cudaError_t launch_batch_fused(const BatchHeader* table, bool all_m4, int factor,
+                                      int grid_limit, cudaStream_t s) {
+  if (all_m4) return launch_persistent(batch_tile_fused_kernel<P, 4>, table, factor, grid_limit, s);
+  return launch_persistent(batch_tile_fused_kernel<P, 0>, table, factor, grid_limit, s);
+}
+
 cudaError_t launch_batch(const BatchHeader* table, int probe_load, int allocate_mode,
                          int integrate_mode, int fuse_mode, int factor, int grid_limit,
-                         cudaStream_t s) {
+                         bool all_m4, cudaStream_t s) {
   cudaError_t e;
   if (fuse_mode == 2) {
     switch (probe_load) {
-      case kLoadL2: return launch_persistent(batch_tile_fused_kernel<kLoadL2>, table, factor, grid_limit, s);
-      case kLoadRelaxed:
-        return launch_persistent(batch_tile_fused_kernel<kLoadRelaxed>, table, factor, grid_limit, s);
-      default:
-        return launch_persistent(batch_tile_fused_kernel<kLoadCached>, table, factor, grid_limit, s);
+      case kLoadL2: return launch_batch_fused<kLoadL2>(table, all_m4, factor, grid_limit, s);
+      case kLoadRelaxed: return launch_batch_fused<kLoadRelaxed>(table, all_m4, factor, grid_limit, s);
+      default: return launch_batch_fused<kLoadCached>(table, all_m4, factor, grid_limit, s);
     }
   }
   if (fuse_mode == 1) {
