@@ -592,8 +592,9 @@ __device__ int warp_insert_get(const VolumeArgs& vol, unsigned long long key, bo
           c[1] = by;
           c[2] = bz;
           // Readers in this pass use the index only to address the pool, never
-          // the coordinates, so no fence is needed before publishing it.
-          atomicExch(&e->idx, static_cast<int>(i));
+          // the coordinates, so no fence is needed before publishing it, and
+          // a plain store is enough (nothing reads the old value).
+          *reinterpret_cast<volatile int*>(&e->idx) = static_cast<int>(i);
           result = static_cast<int>(i);
         }
       }

@@ -379,6 +379,62 @@ __device__ __forceinline__ unsigned pack_sample(int dbx, int dby, int dbz, int l
          static_cast<unsigned>(l);
 }
 
+// The band walk of the fused kernel (the same samples, dedupe and test as
+// walk_point), producing each sample directly in packed form: a rolling
+// window of the two previous voxels replaces the per-sample voxel arrays, so
+// fewer registers are live at once. Packing is relative to the point's first
+// in-range sample. Returns the mask of accepted samples; smp[k] and tv[k]
+// hold the packed voxel and the tsdf value of each accepted sample.
+template <int M>
+__device__ __forceinline__ unsigned walk_point_packed(const FrameArgs& f, const Ray& r,
+                                                      unsigned* smp, float* tv, int& bx0,
+                                                      int& by0, int& bz0) {
+  constexpr int K = 2 * M + 1;
+  int q[K];
+  float zc[K];
+  int ax = 0, ay = 0, az = 0, cx = 0, cy = 0, cz = 0;  // previous two voxels
+  bool a_ok = false, c_ok = false;                     // ... and whether in range
+  bool have_base = false;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const float tk = __fmul_rn(static_cast<float>(k - M), f.v);
+    const float qx = floorf(__fmul_rn(__fmaf_rn(tk, r.dx, r.px), f.inv_v));
+    const float qy = floorf(__fmul_rn(__fmaf_rn(tk, r.dy, r.py), f.inv_v));
+    const float qz = floorf(__fmul_rn(__fmaf_rn(tk, r.dz, r.pz), f.inv_v));
+    const bool ok = (qx >= -kVoxelLimit) && (qx < kVoxelLimit) && (qy >= -kVoxelLimit) &&
+                    (qy < kVoxelLimit) && (qz >= -kVoxelLimit) && (qz < kVoxelLimit);
+    const int gx = ok ? static_cast<int>(qx) : 0;
+    const int gy = ok ? static_cast<int>(qy) : 0;
+    const int gz = ok ? static_cast<int>(qz) : 0;
+    const bool fresh = ok && !(a_ok && gx == ax && gy == ay && gz == az) &&
+                       !(c_ok && gx == cx && gy == cy && gz == cz);
+    cx = ax; cy = ay; cz = az; c_ok = a_ok;
+    ax = gx; ay = gy; az = gz; a_ok = ok;
+    if (ok && !have_base) {
+      bx0 = gx >> 3;
+      by0 = gy >> 3;
+      bz0 = gz >> 3;
+      have_base = true;
+    }
+    q[k] = fresh ? voxel_project(f, gx, gy, gz, zc[k]) : -1;
+    smp[k] = fresh ? pack_sample((gx >> 3) - bx0, (gy >> 3) - by0, (gz >> 3) - bz0,
+                                 local_index(gx, gy, gz))
+                   : 0u;
+  }
+  float d2[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) d2[k] = q[k] >= 0 ? __ldg(f.depth + q[k]) : 0.0f;
+  unsigned acc = 0;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const bool a = q[k] >= 0 && voxel_accept(f, d2[k], zc[k]);
+    acc |= a ? (1u << k) : 0u;
+    tv[k] = a ? tsdf_value(f, r.d, zc[k]) : 0.0f;
+    if (!a) smp[k] = 0u;
+  }
+  return acc;
+}
+
 template <int P, int M>
 __device__ __forceinline__ void tile_fused_body(FusedTileShared& S, const FrameArgs& f,
                                                 const VolumeArgs& vol, int tile, int tiles_x) {
@@ -402,25 +458,24 @@ __device__ __forceinline__ void tile_fused_body(FusedTileShared& S, const FrameA
   int bx0 = 0, by0 = 0, bz0 = 0;
   if constexpr (M > 0) {
     unsigned acc = 0;
-    Walk<M> w;
-    if (valid) acc = walk_point<M>(f, r, w);
-    bool first = true;
+    if (valid) {
+      acc = walk_point_packed<M>(f, r, smp, tv, bx0, by0, bz0);
+    } else {
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        smp[k] = 0u;
+        tv[k] = 0.0f;
+      }
+    }
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      smp[k] = 0u;
-      tv[k] = 0.0f;
-      if ((acc >> k) & 1u) {
-        const int bx = w.gx[k] >> 3, by = w.gy[k] >> 3, bz = w.gz[k] >> 3;
-        if (first) {
-          bx0 = bx;
-          by0 = by;
-          bz0 = bz;
-          first = false;
-        }
-        smp[k] = pack_sample(bx - bx0, by - by0, bz - bz0, local_index(w.gx[k], w.gy[k], w.gz[k]));
-        tv[k] = tsdf_value(f, r.d, w.zc[k]);
-        point_key<kOpFused, P>(pk, pack_key(bx, by, bz), T, vol);
-      }
+      const unsigned q = smp[k];
+      if (q & kSampleValid)
+        point_key<kOpFused, P>(pk,
+                               pack_key(bx0 + static_cast<int>((q >> 9) & 15u) - 8,
+                                        by0 + static_cast<int>((q >> 13) & 15u) - 8,
+                                        bz0 + static_cast<int>((q >> 17) & 15u) - 8),
+                               T, vol);
     }
     tile_list_point_keys<kOpFused, P>(T, vol, pk);
   } else {
