@@ -111,23 +111,27 @@ typedef struct tsdf_layout {
 
 /* Options (tsdf_volume_set_option). */
 typedef enum tsdf_option {
-  /* How stage A reads a probed entry before any compare-exchange (Section 6.2:
-   * a GPU-scope atomic load bypasses L1, a plain load may hit in it).
+  /* How an insert (stage A, or the fused kernels) reads a probed entry before
+   * any compare-exchange (Section 6.2: a GPU-scope atomic load bypasses L1, a
+   * plain load may hit in it).
    * 0 = plain load cached in L1 (default), 1 = L2 only (.cg), 2 = relaxed
    * GPU-scope atomic load. */
   TSDF_OPT_PROBE_LOAD = 0,
   /* Upper bound on the wait for a block index to be published, nanoseconds
    * (default 1e9). The wait gives up with TSDF_ERR_PUBLISH_TIMEOUT. */
   TSDF_OPT_PUBLISH_TIMEOUT_NS = 1,
-  /* Stage B strategy: 0 = each thread looks up its blocks in the table (a
-   * one-entry cache per point) and adds five sums per accepted voxel with
-   * fire-and-forget atomic additions, the paper's update stage (default);
-   * 1 = each warp dedupes its points' blocks with __match_any_sync and looks
-   * them up once, warp-cooperatively, then the same additions. */
+  /* Stage B strategy of the two-stage path (TSDF_OPT_FUSE_MODE 0): 0 = each
+   * thread looks up its blocks in the table (a one-entry cache per point) and
+   * adds the five sums of every accepted voxel with two fire-and-forget
+   * reductions (a 16-byte vector of {tsdf, weight, red, green} and the blue
+   * scalar), the paper's update stage (default); 1 = each warp dedupes its
+   * points' blocks with __match_any_sync and looks them up once,
+   * warp-cooperatively, then the same additions. */
   TSDF_OPT_INTEGRATE_MODE = 2,
   /* Launch shape: threads per CTA for both stages (256). */
   TSDF_OPT_THREADS = 3,
-  /* Stage A strategy: 0 = the paper's protocol as printed (every warp-distinct
+  /* Stage A strategy of the two-stage path (TSDF_OPT_FUSE_MODE 0):
+   * 0 = the paper's protocol as printed (every warp-distinct
    * key inserted as the walk finds it; a thread that finds its key waits for
    * the index to be published); 1 = the distinct keys of each 16x16 pixel
    * tile, via a shared-memory set, inserted warp-cooperatively after one

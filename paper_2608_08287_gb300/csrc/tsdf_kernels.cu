@@ -1,23 +1,30 @@
 // Kernels of hash-blocked TSDF fusion (paper Section 2.2, "Two passes").
 //
-// warp_kernel<Op> (default for every operation): each warp covers an 8x4 pixel
-// patch and works alone, with no shared memory and no barriers --
-//   1. every lane walks its point's band (unrolled when the half band M is
-//      compiled) and keeps each accepted voxel packed with its tsdf value;
-//   2. the warp dedupes the first three distinct blocks of every point with
-//      __match_any_sync, compacts the leaders' keys into lanes and resolves
-//      them in one warp-cooperative pass: stage A inserts (Listing 1 probe and
-//      compare-exchange, counter increments aggregated per warp, no waiting),
-//      stage B looks up, the fused kernel inserts and obtains the indices;
-//   3. stage B and the fused kernel add five sums per accepted voxel with
-//      fire-and-forget reductions.
-// tile_allocate_kernel: stage A with a shared-memory key set per 16x16 tile.
-// The paper's own shapes are kept as strategy 0 of each stage:
-//   allocate_kernel: Listing 1 per sample after a warp dedupe, waiting for
-//     publication on a hit;
-//   integrate_scatter_kernel: per-thread lookups and five atomic additions per
-//     accepted voxel.
-// Read-out and reset: export_kernel (means from sums), clear_used_kernel.
+// tile_fused_kernel (the default path, one launch per frame): one CTA per
+// 16x16 pixel tile --
+//   1. every thread walks its point's band once (unrolled when the half band
+//      M is compiled), keeps each accepted sample as one packed word and its
+//      tsdf value, and the tile's distinct blocks are collected in a
+//      shared-memory set and list (a per-warp __match_any_sync dedupe first);
+//   2. the list is inserted warp-cooperatively (Listing 1 probe and
+//      compare-exchange, counter increments aggregated per warp) and every
+//      block's pool index obtained into shared memory;
+//   3. every accepted voxel's five sums are added with two fire-and-forget
+//      reductions (a 16-byte vector and a scalar), the index taken from the
+//      tile's list: no second walk, no table probe.
+// The two-pass path of the paper is kept as separate stage A and stage B
+// kernels, each with several strategies:
+//   stage A: allocate_kernel (Listing 1 per sample after a warp dedupe,
+//     waiting for publication on a hit: the paper's protocol),
+//     tile_allocate_kernel (phases 1 and 2 above, without waiting),
+//     warp_kernel<Allocate> (per warp, no shared memory);
+//   stage B: integrate_scatter_kernel (per-thread lookups, the paper's
+//     update), warp_kernel<Integrate> (warp-deduped lookups);
+//   warp_kernel<Fused>: a barrier-free fused kernel, one warp per 8x4 patch.
+// Batched persistent variants serve many frames, each into its own volume,
+// per launch. Read-out, reset and diagnostics: export_kernel (means from
+// sums), slot_list_kernel, clear_used_kernel / clear_slots_kernel,
+// table_stats_kernel, weight_sum_kernel; surface extraction: extract_kernel.
 
 #include <algorithm>
 #include <climits>
