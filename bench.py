@@ -154,10 +154,16 @@ class ClockSampler:
 # traffic from a committed ncu summary, valid only for the current kernel source
 # ----------------------------------------------------------------------------
 def kernel_source_hash():
+    """Hash of the device code (comments and blank space removed, so that
+    documentation edits do not invalidate a capture of the same kernels)."""
+    import re
     h = hashlib.sha256()
     for f in ("tsdf_device.cuh", "tsdf_kernels.cu"):
-        with open(os.path.join(ROOT, "paper_2608_08287_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2608_08287_gb300", "csrc", f)) as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        h.update("".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 
