@@ -704,7 +704,7 @@ def cpu_baseline(seconds):
     import oracle
     from paper_2608_08287_gb300 import synth
     spec = synth.ROOM_640
-    frames = make_frames(0)[:2]
+    frames = make_frames(0)       # the GPU arm's frames and config
     n = 0
     points = 0
     t0 = time.perf_counter()
@@ -729,7 +729,7 @@ def run_reference(args):
     from paper_2608_08287_gb300 import synth
     oracle.build()
     spec = synth.ROOM_640
-    frames = make_frames(0)[:2]
+    frames = make_frames(0)       # the GPU arm's frames and config
 
     def step(i):
         f = frames[i % len(frames)]
@@ -745,7 +745,8 @@ def run_reference(args):
     points = sum(step(args.warmup + i) for i in range(args.steps))
     el = time.perf_counter() - t0
     value = points / el
-    return {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": 0,
+    return {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": args.gpus,
+            "device": "host CPU, one thread (the oracle; no GPU is used)",
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(el / args.steps * 1e3, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
