@@ -311,6 +311,75 @@ __device__ __forceinline__ int local_index(int gx, int gy, int gz) {
   return (gx & 7) | ((gy & 7) << 3) | ((gz & 7) << 6);
 }
 
+// A band sample packed in one word: accepted flag, the block's offset from
+// the block of the point's first in-range sample (4 bits per axis,
+// biased by 8: a band of at most 2*16+1 samples, one voxel apart, crosses at
+// most four block boundaries per axis) and the voxel's local index.
+constexpr unsigned kSampleValid = 1u << 31;
+
+__device__ __forceinline__ unsigned pack_sample(int dbx, int dby, int dbz, int l) {
+  return kSampleValid | (static_cast<unsigned>(dbx + 8) << 9) |
+         (static_cast<unsigned>(dby + 8) << 13) | (static_cast<unsigned>(dbz + 8) << 17) |
+         static_cast<unsigned>(l);
+}
+
+// The band walk (the same samples, dedupe and test as walk_point), producing
+// each sample directly in packed form: a rolling window of the two previous
+// voxels replaces the per-sample voxel arrays, so fewer registers are live at
+// once. Packing is relative to the point's first
+// in-range sample. Returns the mask of accepted samples; smp[k] and (with
+// TSDF) tv[k] hold the packed voxel and the tsdf value of each accepted sample.
+template <int M, bool TSDF = true>
+__device__ __forceinline__ unsigned walk_point_packed(const FrameArgs& f, const Ray& r,
+                                                      unsigned* smp, float* tv, int& bx0,
+                                                      int& by0, int& bz0) {
+  constexpr int K = 2 * M + 1;
+  int q[K];
+  float zc[K];
+  int ax = 0, ay = 0, az = 0, cx = 0, cy = 0, cz = 0;  // previous two voxels
+  bool a_ok = false, c_ok = false;                     // ... and whether in range
+  bool have_base = false;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const float tk = __fmul_rn(static_cast<float>(k - M), f.v);
+    const float qx = floorf(__fmul_rn(__fmaf_rn(tk, r.dx, r.px), f.inv_v));
+    const float qy = floorf(__fmul_rn(__fmaf_rn(tk, r.dy, r.py), f.inv_v));
+    const float qz = floorf(__fmul_rn(__fmaf_rn(tk, r.dz, r.pz), f.inv_v));
+    const bool ok = (qx >= -kVoxelLimit) && (qx < kVoxelLimit) && (qy >= -kVoxelLimit) &&
+                    (qy < kVoxelLimit) && (qz >= -kVoxelLimit) && (qz < kVoxelLimit);
+    const int gx = ok ? static_cast<int>(qx) : 0;
+    const int gy = ok ? static_cast<int>(qy) : 0;
+    const int gz = ok ? static_cast<int>(qz) : 0;
+    const bool fresh = ok && !(a_ok && gx == ax && gy == ay && gz == az) &&
+                       !(c_ok && gx == cx && gy == cy && gz == cz);
+    cx = ax; cy = ay; cz = az; c_ok = a_ok;
+    ax = gx; ay = gy; az = gz; a_ok = ok;
+    if (ok && !have_base) {
+      bx0 = gx >> 3;
+      by0 = gy >> 3;
+      bz0 = gz >> 3;
+      have_base = true;
+    }
+    q[k] = fresh ? voxel_project(f, gx, gy, gz, zc[k]) : -1;
+    smp[k] = fresh ? pack_sample((gx >> 3) - bx0, (gy >> 3) - by0, (gz >> 3) - bz0,
+                                 local_index(gx, gy, gz))
+                   : 0u;
+  }
+  float d2[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) d2[k] = q[k] >= 0 ? __ldg(f.depth + q[k]) : 0.0f;
+  unsigned acc = 0;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const bool a = q[k] >= 0 && voxel_accept(f, d2[k], zc[k]);
+    acc |= a ? (1u << k) : 0u;
+    if (TSDF) tv[k] = a ? tsdf_value(f, r.d, zc[k]) : 0.0f;
+    if (!a) smp[k] = 0u;
+  }
+  return acc;
+}
+
+
 // ----------------------------------------------------------------------------
 // table access
 // ----------------------------------------------------------------------------
