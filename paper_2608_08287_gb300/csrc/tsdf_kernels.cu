@@ -1569,17 +1569,21 @@ static int persistent_grid(K kernel, int factor) {
   struct Shape {
     int sms = 0, occ = 0;
   };
-  static Shape shape;  // one per kernel instantiation
-  if (shape.sms == 0) {
+  // One per kernel instantiation, computed once (thread-safe static
+  // initialisation) for the device current at the first call; a zero shape
+  // (a failed query) makes the launch fail with an invalid configuration.
+  static const Shape shape = [kernel]() {
+    Shape sh;
     int dev = 0, sms = 0, occ = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return sh;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-      return 0;
+      return sh;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kThreads, 0) != cudaSuccess)
-      return 0;
-    shape.occ = occ < 1 ? 1 : occ;
-    shape.sms = sms;
-  }
+      return sh;
+    sh.occ = occ < 1 ? 1 : occ;
+    sh.sms = sms;
+    return sh;
+  }();
   const int occ = (factor > 0 && factor < shape.occ) ? factor : shape.occ;
   return occ * shape.sms;
 }
