@@ -95,3 +95,34 @@ def test_status_strings_and_version(L):
         assert tsdf.tsdf_status_string(code) == want
     assert "sm_103a" in tsdf.tsdf_version()
     assert tsdf.tsdf_launch_count() == 0
+
+
+STRUCTS = ("tsdf_intrinsics", "tsdf_pose", "tsdf_layout", "tsdf_frame", "tsdf_request",
+           "tsdf_completion", "tsdf_table_stats", "tsdf_tuning", "tsdf_extract_timing")
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """Every struct the binding mirrors has the size and field offsets the C
+    compiler gives it from include/tsdf.h (a C program prints them)."""
+    import ctypes
+    import subprocess
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "tsdf.h"', 'int main(void) {']
+    for name in STRUCTS:
+        cls = getattr(tsdf, name)
+        lines.append(f'  printf("{name} %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'  printf("{name}.{field} %zu\\n", offsetof({name}, {field}));')
+    lines += ['  return 0;', '}']
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+                    str(exe)], check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True,
+                                                         text=True, check=True).stdout.split("\n")
+               if line)
+    for name in STRUCTS:
+        cls = getattr(tsdf, name)
+        assert int(got[name]) == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert int(got[f"{name}.{field}"]) == getattr(cls, field).offset, (name, field)
