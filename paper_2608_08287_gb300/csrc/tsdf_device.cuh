@@ -510,6 +510,70 @@ __device__ int insert_block(const VolumeArgs& vol, unsigned long long key, int b
   return -1;
 }
 
+// Long probe chains, warp-cooperatively (at high load the multiply-xor hash
+// leaves long clusters of occupied slots; probing them one slot per step
+// costs one round trip per slot). Every lane of the warp calls it after a
+// probe step. Each lane that has already probed kCoopAfter slots or more
+// without finishing is taken in turn: the 32 lanes read 32 consecutive slots
+// of its chain at once, and its slot jumps to the first one that holds its
+// key or is empty -- the slot sequential probing would stop at, since an
+// occupied slot never changes (a stale EMPTY read only makes it stop early,
+// and the step then re-examines the slot). The scan never passes the probe
+// limit.
+constexpr unsigned kCoopAfter = 4;
+
+__device__ __forceinline__ void warp_skip_long_chains(const VolumeArgs& vol,
+                                                      unsigned long long key, bool& todo,
+                                                      unsigned int& s, unsigned int& probe) {
+  const unsigned lane = threadIdx.x & 31u;
+  unsigned longs = __ballot_sync(0xffffffffu, todo && probe >= kCoopAfter);
+  while (longs) {
+    const int L = __ffs(longs) - 1;
+    longs &= longs - 1;
+    const unsigned long long lkey = __shfl_sync(0xffffffffu, key, L);
+    unsigned int ls = __shfl_sync(0xffffffffu, s, L);
+    unsigned int lprobe = __shfl_sync(0xffffffffu, probe, L);
+    bool found = false, stopped = false;
+    for (unsigned int step = 0; !found && lprobe < vol.probe_limit; ++step) {
+      // a poisoned volume stops long scans early (every 8 windows)
+      if ((step & 7u) == 7u &&
+          (load_err_volatile(vol.hdr) & (TSDF_ERRBIT_POOL_FULL | TSDF_ERRBIT_TABLE_FULL))) {
+        stopped = true;
+        break;
+      }
+      const unsigned int left = vol.probe_limit - lprobe;
+      const unsigned int window = left < 32u ? left : 32u;
+      unsigned long long k = 0;
+      if (lane < window) {
+        asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];"
+                     : "=l"(k)
+                     : "l"(&vol.table[(ls + lane) & vol.mask].key)
+                     : "memory");
+      }
+      const unsigned stop = __ballot_sync(0xffffffffu, lane < window && (k == kEmptyKey || k == lkey));
+      if (stop) {
+        const unsigned off = static_cast<unsigned>(__ffs(stop) - 1);
+        ls = (ls + off) & vol.mask;
+        lprobe += off;
+        found = true;
+      } else {
+        ls = (ls + window) & vol.mask;
+        lprobe += window;
+      }
+    }
+    if (static_cast<int>(lane) == L) {
+      s = ls;
+      probe = lprobe;
+      if (stopped) {
+        todo = false;
+      } else if (!found) {
+        probe_exhausted(vol);
+        todo = false;
+      }
+    }
+  }
+}
+
 // Stage A insert without waiting, warp-cooperative: every lane of the warp
 // calls it, each with at most one key (`has`). The probe and compare-exchange
 // follow Listing 1 (Section 2.3) with the lost-CAS reading (re-examine the
@@ -529,7 +593,7 @@ __device__ void warp_insert_nowait(const VolumeArgs& vol, unsigned long long key
   if (has) unpack_key(key, bx, by, bz);
   unsigned int s = has ? (hash_block(bx, by, bz) & vol.mask) : 0u;
   bool todo = has;
-  unsigned int probe = 0;
+  unsigned int probe = 0, rounds = 0;
   while (__any_sync(0xffffffffu, todo)) {
     bool won = false;
     Entry* e = vol.table + s;
@@ -585,6 +649,8 @@ __device__ void warp_insert_nowait(const VolumeArgs& vol, unsigned long long key
         }
       }
     }
+    // (a warp-uniform gate: short chains, the common case, never pay for it)
+    if (++rounds >= kCoopAfter) warp_skip_long_chains(vol, key, todo, s, probe);
   }
 }
 
@@ -599,7 +665,7 @@ __device__ int warp_insert_get(const VolumeArgs& vol, unsigned long long key, bo
   if (has) unpack_key(key, bx, by, bz);
   unsigned int s = has ? (hash_block(bx, by, bz) & vol.mask) : 0u;
   bool todo = has;
-  unsigned int probe = 0;
+  unsigned int probe = 0, rounds = 0;
   int result = -1;
   const Entry* hit = nullptr;
   while (__any_sync(0xffffffffu, todo)) {
@@ -668,6 +734,8 @@ __device__ int warp_insert_get(const VolumeArgs& vol, unsigned long long key, bo
         }
       }
     }
+    // (a warp-uniform gate: short chains, the common case, never pay for it)
+    if (++rounds >= kCoopAfter) warp_skip_long_chains(vol, key, todo, s, probe);
   }
   if (hit) result = wait_published(vol, hit);
   return result;
