@@ -158,7 +158,7 @@ def kernel_source_hash():
     documentation edits do not invalidate a capture of the same kernels)."""
     import re
     h = hashlib.sha256()
-    for f in ("tsdf_device.cuh", "tsdf_kernels.cu"):
+    for f in ("tsdf_device.cuh", "tsdf_tile.cuh", "tsdf_kernels.cu", "tsdf_kernels_split.cu"):
         with open(os.path.join(ROOT, "paper_2608_08287_gb300", "csrc", f)) as fh:
             text = fh.read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
@@ -368,6 +368,10 @@ def run_gpu(args, rank, world, local_rank):
                 extra["load_sweep"] = run_load_sweep(args, torch, tsdf, sweep_frames)
             except Exception as e:  # noqa: BLE001
                 extra["load_sweep"] = {"error": repr(e)}
+        try:
+            extra["small_frames"] = run_small_frames(args, torch, tsdf)
+        except Exception as e:  # noqa: BLE001
+            extra["small_frames"] = {"error": repr(e)}
 
     out = None
     if rank == 0:
@@ -404,6 +408,12 @@ def run_gpu(args, rank, world, local_rank):
         }
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+            if not args.headline_only:
+                try:
+                    out["cpu_baseline"]["multicore"] = cpu_baseline_multicore(
+                        args.cpu_seconds)
+                except Exception as e:  # noqa: BLE001
+                    out["cpu_baseline"]["multicore"] = {"error": repr(e)}
     return out
 
 
@@ -486,10 +496,8 @@ def run_batched(args, torch, tsdf, serving, bank):
     2^16..2^20), one frame each per step into fresh volumes, as one batch
     (persistent launches replayed from a CUDA graph) against a loop of
     per-frame launches. Device time per step, L2 scrubbed between steps."""
-    from paper_2608_08287_gb300 import synth
-    n = 64
-    u = synth.uniform(20261208, 1, n)
-    res = [list(serving.SESSION_CLASSES)[int(x * 3) % 3] for x in u]
+    n = BATCH_SESSIONS
+    res = batch_resolutions(n)
     vols = []
     for r in res:
         sp = serving.SESSION_CLASSES[r]
@@ -587,6 +595,60 @@ def run_serving(args, torch, serving, bank):
             torch.cuda.synchronize()
             into[name] = res.summary()
             into[name]["status"] = st
+    return out
+
+
+def run_small_frames(args, torch, tsdf):
+    """Frames too small to fill the GPU with one thread per point: the
+    160x120 plane-and-sphere frame (voxel 1 cm, truncation 4 cm, 2^16 slots,
+    pool 2^14) and a 320x240 room frame (1 cm / 4 cm, 2^18 slots, pool 2^16),
+    each fused into an empty volume by the fused tile kernel with 1, 2, 4 and
+    8 threads per point, and what tsdf_autotune_frame picks. Device time per
+    step (CUDA events), L2 scrubbed and volume reset between steps."""
+    from paper_2608_08287_gb300 import synth
+    cases = [("plane_sphere_160x120", synth.plane_sphere_frame(), synth.PLANE_SPHERE_160),
+             ("room_320x240", synth.room_frame(12, width=320, height=240),
+              synth.VolumeSpec(0.01, 0.04, 1 << 18, 1 << 16))]
+    stream = torch.cuda.Stream()
+    sp = stream.cuda_stream
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    scrub = torch.ones(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    steps = max(20, args.small_steps)
+    out = {"timed": f"median of {steps} steps after 5 warm-up, L2 scrubbed, empty volume"}
+    for name, f, spec in cases:
+        d = torch.from_numpy(f.depth).cuda()
+        c = torch.from_numpy(f.rgb).cuda()
+        intr, pose = tsdf.intrinsics(f.intr), tsdf.pose_struct(f.pose)
+        vol = tsdf.Volume(spec.voxel_size, spec.truncation, spec.table_slots, spec.pool_blocks)
+        row = {"points": int(f.valid_points)}
+        for tpp in (1, 2, 4, 8):
+            assert vol.set_option("threads_per_point", tpp) == "OK"
+            ms = []
+            for i in range(5 + steps):
+                vol.reset(sp)
+                with torch.cuda.stream(stream):
+                    l2_scrub(flush, scrub, i)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                assert tsdf.tsdf_fuse_frame_async(vol.handle, d, f.depth.shape[1],
+                                                  f.depth.shape[0], intr, pose, c, sp) == "OK"
+                e1.record(stream)
+                stream.synchronize()
+                if i >= 5:
+                    ms.append(e0.elapsed_time(e1))
+            assert vol.status(sp) == "OK"
+            med = float(np.median(ms))
+            row[f"tpp{tpp}_ms"] = round(med, 5)
+            row[f"tpp{tpp}_pts_per_s"] = round(f.valid_points / (med / 1e3), 1)
+        assert vol.set_option("threads_per_point", 1) == "OK"
+        assert vol.reset(sp) == "OK"
+        st, tuning = vol.autotune(d, f.intr, f.pose, c, reps=10, stream=sp)
+        assert st == "OK", st
+        row["autotune"] = {k: tuning[k] for k in ("fuse_mode", "probe_load", "threads_per_point",
+                                                  "best_ms", "default_ms", "candidates")}
+        vol.close()
+        out[name] = row
+    del flush, scrub
     return out
 
 
@@ -729,6 +791,63 @@ def cpu_baseline(seconds):
             "sample": f"{n} whole 640x480 room frames into empty volumes, one thread"}
 
 
+BATCH_SESSIONS = 64
+
+
+def batch_resolutions(n=BATCH_SESSIONS):
+    """The batched workload's per-session resolutions (seeded)."""
+    from paper_2608_08287_gb300 import serving, synth
+    u = synth.uniform(20261208, 1, n)
+    return [list(serving.SESSION_CLASSES)[int(x * 3) % 3] for x in u]
+
+
+def _oracle_sessions_worker(worker, cores, seconds):
+    """One host core's share of the batched workload: sessions worker,
+    worker + cores, ... each fuse their frame into a fresh oracle volume, in
+    turn, until `seconds` have passed. Frames are rendered before the clock
+    starts. Returns (points, frames, elapsed)."""
+    import oracle
+    from paper_2608_08287_gb300 import serving, synth
+    res = batch_resolutions()
+    mine = []
+    for i in range(worker, len(res), cores):
+        w, h = res[i]
+        mine.append((serving.SESSION_CLASSES[res[i]], synth.room_frame(12 * (i % 24), width=w,
+                                                                      height=h)))
+    points = frames = 0
+    t0 = time.perf_counter()
+    while mine:
+        spec, f = mine[frames % len(mine)]
+        ov = oracle.OracleVolume(spec.voxel_size, spec.truncation, spec.table_slots,
+                                 spec.pool_blocks)
+        assert ov.fuse_frame(f) == "OK"
+        ov.close()
+        frames += 1
+        points += f.valid_points
+        if time.perf_counter() - t0 >= seconds:
+            break
+    return points, frames, time.perf_counter() - t0
+
+
+def cpu_baseline_multicore(seconds):
+    """One oracle instance per host core over the batched workload's sessions
+    (independent volumes, so embarrassingly parallel): points of all cores over
+    the slowest core's time. A process pool started with spawn."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.starmap(_oracle_sessions_worker,
+                           [(w, cores, seconds) for w in range(cores)])
+    points = sum(r[0] for r in res)
+    frames = sum(r[1] for r in res)
+    el = max(r[2] for r in res)
+    return {"value": round(points / el, 1), "unit": UNIT, "cores": cores,
+            "kind": "oracle, one instance per core",
+            "sample": f"{frames} frames of the {BATCH_SESSIONS}-session batched workload "
+                      "(mixed 160x120 / 320x240 / 640x480 room frames), each into a fresh "
+                      f"volume, about {seconds:g} s per core"}
+
+
 def run_reference(args):
     """--impl reference: the CPU oracle timed on the same workload and metric."""
     import oracle
@@ -792,6 +911,8 @@ def main():
     ap.add_argument("--sweep-frames", type=int, default=142,
                     help="orbit frames rendered for the load-factor sweep (0 = no sweep)")
     ap.add_argument("--sweep-reps", type=int, default=10)
+    ap.add_argument("--small-steps", type=int, default=100,
+                    help="timed steps per threads-per-point setting on the small frames")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

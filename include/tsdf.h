@@ -175,7 +175,17 @@ typedef enum tsdf_option {
    * probe loop with a compile-time trip count (Section 7, the bounded probe
    * of the Triton arm). It exists to measure that loss against the unbounded
    * probe. Values above table_slots act as unbounded. */
-  TSDF_OPT_PROBE_BOUND = 9
+  TSDF_OPT_PROBE_BOUND = 9,
+  /* Threads per depth point in the fused tile kernel (TSDF_OPT_FUSE_MODE 2;
+   * other modes ignore it): 1 (default) = each thread walks its point's whole
+   * band; 2, 4 or 8 = the point's 2M+1 band samples are split into that many
+   * contiguous spans, one per thread, so a frame runs on that many times more
+   * threads (for small frames that do not fill the GPU). The result is the
+   * same. Values above 1 need the default TSDF_OPT_PROBE_LOAD and a half band
+   * M = round(truncation / voxel_size) of 2, 4 or 8; TSDF_ERR_INVALID_ARG
+   * otherwise, and setting another probe load while it is above 1 is
+   * rejected too. Not a batch option. */
+  TSDF_OPT_THREADS_PER_POINT = 10
 } tsdf_option;
 
 /* ---------------------------------------------------------------------------
@@ -346,10 +356,13 @@ typedef struct tsdf_tuning {
   int candidates;             /* configurations timed */
   float best_ms;              /* median time of the chosen configuration */
   float default_ms;           /* median time of the default configuration */
+  int threads_per_point;      /* volumes: the chosen TSDF_OPT_THREADS_PER_POINT (1 for a batch) */
 } tsdf_tuning;
 
 /* Tune `vol` for this frame: every stage A x stage B strategy, the fused
- * kernel and the probe loads, each fusing the frame into a scratch copy of the
+ * kernels, the probe loads and (where the half band allows it) 2, 4 and 8
+ * threads per point in the fused tile kernel, each fusing the frame into a
+ * scratch copy of the
  * volume's current state (restored before every repetition). The volume's
  * contents are not modified; its options are set to the fastest
  * configuration, which *out describes. Needs device memory for one more

@@ -267,6 +267,8 @@ tsdf_status tsdf_volume_set_option(tsdf_volume* vol, tsdf_option opt, int64_t va
   switch (opt) {
     case TSDF_OPT_PROBE_LOAD:
       if (value < 0 || value > 2) return TSDF_ERR_INVALID_ARG;
+      if (value != tsdf::kLoadCached && vol->threads_per_point != 1)
+        return TSDF_ERR_INVALID_ARG;  // the split walk exists for the default load only
       vol->probe_load = static_cast<int>(value);
       return TSDF_OK;
     case TSDF_OPT_PUBLISH_TIMEOUT_NS:
@@ -295,6 +297,13 @@ tsdf_status tsdf_volume_set_option(tsdf_volume* vol, tsdf_option opt, int64_t va
       if (vol->dirty && static_cast<unsigned int>(value) != vol->va.slot_index)
         return TSDF_ERR_INVALID_ARG;  // the layout of the stored blocks would change
       vol->va.slot_index = static_cast<unsigned int>(value);
+      return TSDF_OK;
+    case TSDF_OPT_THREADS_PER_POINT:
+      if (value != 1 && value != 2 && value != 4 && value != 8) return TSDF_ERR_INVALID_ARG;
+      if (value != 1 && (vol->probe_load != tsdf::kLoadCached ||
+                         (vol->half_band != 2 && vol->half_band != 4 && vol->half_band != 8)))
+        return TSDF_ERR_INVALID_ARG;
+      vol->threads_per_point = static_cast<int>(value);
       return TSDF_OK;
     case TSDF_OPT_PROBE_BOUND:
       if (value < 0) return TSDF_ERR_INVALID_ARG;
@@ -362,7 +371,8 @@ tsdf_status tsdf_fuse_frame_async(tsdf_volume* vol, const float* depth_dev, int 
   vol->dirty = true;
   if (vol->fuse_mode != 0)
     return from_cuda(
-        tsdf::launch_fused(f, vol->va, vol->probe_load, vol->fuse_mode, as_stream(stream)));
+        tsdf::launch_fused(f, vol->va, vol->probe_load, vol->fuse_mode,
+                           vol->fuse_mode == 2 ? vol->threads_per_point : 1, as_stream(stream)));
   cudaError_t e = tsdf::launch_allocate(f, vol->va, vol->probe_load, vol->allocate_mode,
                                         as_stream(stream));
   if (e == cudaSuccess) e = tsdf::launch_integrate(f, vol->va, vol->integrate_mode,

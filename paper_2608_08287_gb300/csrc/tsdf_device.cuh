@@ -323,30 +323,35 @@ __device__ __forceinline__ unsigned pack_sample(int dbx, int dby, int dbz, int l
          static_cast<unsigned>(l);
 }
 
-// The band walk (the same samples, dedupe and test as walk_point), producing
-// each sample directly in packed form: a rolling window of the two previous
-// voxels replaces the per-sample voxel arrays, so fewer registers are live at
-// once. Packing is relative to the point's first
-// in-range sample. Returns the mask of accepted samples; smp[k] and (with
-// TSDF) tv[k] hold the packed voxel and the tsdf value of each accepted sample.
-template <int M, bool TSDF = true>
-__device__ __forceinline__ unsigned walk_point_packed(const FrameArgs& f, const Ray& r,
-                                                      unsigned* smp, float* tv, int& bx0,
-                                                      int& by0, int& bz0) {
-  constexpr int K = 2 * M + 1;
-  int q[K];
-  float zc[K];
+// The band walk over samples lo .. lo+n-1 of one point (n <= C): the same
+// samples, dedupe and test as walk_point, each sample produced directly in
+// packed form. A rolling window of the two previous voxels replaces the
+// per-sample voxel arrays, so fewer registers are live at once; it starts two
+// samples before lo, so a walk split into spans over several threads dedupes
+// exactly as the whole walk does. Packing is relative to the block of the
+// span's first in-range sample. Returns the mask of accepted samples (bit i
+// for sample lo+i); smp[i] and (with TSDF) tv[i] hold the packed voxel and the
+// tsdf value of each accepted one.
+template <int M, int C, bool TSDF = true>
+__device__ __forceinline__ unsigned walk_point_span(const FrameArgs& f, const Ray& r, int lo,
+                                                    int n, unsigned* smp, float* tv, int& bx0,
+                                                    int& by0, int& bz0) {
+  int q[C];
+  float zc[C];
   int ax = 0, ay = 0, az = 0, cx = 0, cy = 0, cz = 0;  // previous two voxels
   bool a_ok = false, c_ok = false;                     // ... and whether in range
   bool have_base = false;
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
+  for (int i = -2; i < C; ++i) {
+    const int k = lo + i;
     const float tk = __fmul_rn(static_cast<float>(k - M), f.v);
     const float qx = floorf(__fmul_rn(__fmaf_rn(tk, r.dx, r.px), f.inv_v));
     const float qy = floorf(__fmul_rn(__fmaf_rn(tk, r.dy, r.py), f.inv_v));
     const float qz = floorf(__fmul_rn(__fmaf_rn(tk, r.dz, r.pz), f.inv_v));
-    const bool ok = (qx >= -kVoxelLimit) && (qx < kVoxelLimit) && (qy >= -kVoxelLimit) &&
-                    (qy < kVoxelLimit) && (qz >= -kVoxelLimit) && (qz < kVoxelLimit);
+    // samples before the band or past the span are never in range
+    const bool ok = k >= 0 && i < n && (qx >= -kVoxelLimit) && (qx < kVoxelLimit) &&
+                    (qy >= -kVoxelLimit) && (qy < kVoxelLimit) && (qz >= -kVoxelLimit) &&
+                    (qz < kVoxelLimit);
     const int gx = ok ? static_cast<int>(qx) : 0;
     const int gy = ok ? static_cast<int>(qy) : 0;
     const int gz = ok ? static_cast<int>(qz) : 0;
@@ -354,29 +359,38 @@ __device__ __forceinline__ unsigned walk_point_packed(const FrameArgs& f, const 
                        !(c_ok && gx == cx && gy == cy && gz == cz);
     cx = ax; cy = ay; cz = az; c_ok = a_ok;
     ax = gx; ay = gy; az = gz; a_ok = ok;
+    if (i < 0) continue;  // the window's lead-in: voxel only
     if (ok && !have_base) {
       bx0 = gx >> 3;
       by0 = gy >> 3;
       bz0 = gz >> 3;
       have_base = true;
     }
-    q[k] = fresh ? voxel_project(f, gx, gy, gz, zc[k]) : -1;
-    smp[k] = fresh ? pack_sample((gx >> 3) - bx0, (gy >> 3) - by0, (gz >> 3) - bz0,
+    q[i] = fresh ? voxel_project(f, gx, gy, gz, zc[i]) : -1;
+    smp[i] = fresh ? pack_sample((gx >> 3) - bx0, (gy >> 3) - by0, (gz >> 3) - bz0,
                                  local_index(gx, gy, gz))
                    : 0u;
   }
-  float d2[K];
+  float d2[C];
 #pragma unroll
-  for (int k = 0; k < K; ++k) d2[k] = q[k] >= 0 ? __ldg(f.depth + q[k]) : 0.0f;
+  for (int i = 0; i < C; ++i) d2[i] = q[i] >= 0 ? __ldg(f.depth + q[i]) : 0.0f;
   unsigned acc = 0;
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
-    const bool a = q[k] >= 0 && voxel_accept(f, d2[k], zc[k]);
-    acc |= a ? (1u << k) : 0u;
-    if (TSDF) tv[k] = a ? tsdf_value(f, r.d, zc[k]) : 0.0f;
-    if (!a) smp[k] = 0u;
+  for (int i = 0; i < C; ++i) {
+    const bool a = q[i] >= 0 && voxel_accept(f, d2[i], zc[i]);
+    acc |= a ? (1u << i) : 0u;
+    if (TSDF) tv[i] = a ? tsdf_value(f, r.d, zc[i]) : 0.0f;
+    if (!a) smp[i] = 0u;
   }
   return acc;
+}
+
+// The whole band walk of one point in packed form (all 2M+1 samples).
+template <int M, bool TSDF = true>
+__device__ __forceinline__ unsigned walk_point_packed(const FrameArgs& f, const Ray& r,
+                                                      unsigned* smp, float* tv, int& bx0,
+                                                      int& by0, int& bz0) {
+  return walk_point_span<M, 2 * M + 1, TSDF>(f, r, 0, 2 * M + 1, smp, tv, bx0, by0, bz0);
 }
 
 

@@ -15,8 +15,15 @@ cudaError_t launch_allocate(const FrameArgs& f, const VolumeArgs& vol, int probe
                             cudaStream_t s);
 cudaError_t launch_integrate(const FrameArgs& f, const VolumeArgs& vol, int mode,
                              cudaStream_t s);
+// The fused path. threads_per_point > 1 (2, 4 or 8) takes the fused tile
+// kernel with each point's walk split over that many threads; it exists for
+// fuse mode 2, the default probe load and half bands 2, 4 and 8
+// (cudaErrorInvalidValue otherwise).
 cudaError_t launch_fused(const FrameArgs& f, const VolumeArgs& vol, int probe_load, int mode,
-                         cudaStream_t s);
+                         int threads_per_point, cudaStream_t s);
+// The split-walk fused tile kernels (their own translation unit).
+cudaError_t launch_fused_split(const FrameArgs& f, const VolumeArgs& vol, int threads_per_point,
+                               cudaStream_t s);
 // Batched launches (all frames of a session table): allocate + integrate, or
 // the fused kernel. factor caps the resident CTAs per SM (0 = as many as fit).
 // grid_limit > 0 caps the grid (e.g. at the batch's tile count). all_m4: every

@@ -1,5 +1,6 @@
-// Autotuning: time every fusion strategy (and, for batches, the launch shape)
-// on the caller's own frames and keep the fastest.
+// Autotuning: time every fusion strategy (and, for batches, the launch shape;
+// for a volume, the threads per point of the fused tile kernel) on the
+// caller's own frames and keep the fastest.
 //
 // A single volume is tuned on a scratch copy of itself: before every timed
 // repetition the scratch is restored from the volume (tsdf_volume_copy) and
@@ -27,6 +28,7 @@ namespace {
 
 struct Config {
   int allocate_mode, integrate_mode, fuse_mode, probe_load, ctas_per_sm, use_graph;
+  int threads_per_point = 1;
 };
 
 float median(std::vector<float> v) {
@@ -66,10 +68,14 @@ struct Events {
 };
 
 tsdf_status apply_volume(tsdf_volume* v, const Config& c) {
-  tsdf_status st = tsdf_volume_set_option(v, TSDF_OPT_ALLOCATE_MODE, c.allocate_mode);
+  // one thread per point first: the probe load may only change then
+  tsdf_status st = tsdf_volume_set_option(v, TSDF_OPT_THREADS_PER_POINT, 1);
+  if (st == TSDF_OK) st = tsdf_volume_set_option(v, TSDF_OPT_ALLOCATE_MODE, c.allocate_mode);
   if (st == TSDF_OK) st = tsdf_volume_set_option(v, TSDF_OPT_INTEGRATE_MODE, c.integrate_mode);
   if (st == TSDF_OK) st = tsdf_volume_set_option(v, TSDF_OPT_FUSE_MODE, c.fuse_mode);
   if (st == TSDF_OK) st = tsdf_volume_set_option(v, TSDF_OPT_PROBE_LOAD, c.probe_load);
+  if (st == TSDF_OK)
+    st = tsdf_volume_set_option(v, TSDF_OPT_THREADS_PER_POINT, c.threads_per_point);
   return st;
 }
 
@@ -93,6 +99,7 @@ void fill(tsdf_tuning* out, const Config& c, float best, float dflt, int n) {
   out->candidates = n;
   out->best_ms = best;
   out->default_ms = dflt;
+  out->threads_per_point = c.threads_per_point;
 }
 
 }  // namespace
@@ -122,14 +129,17 @@ tsdf_status tsdf_autotune_frame(tsdf_volume* vol, const float* depth_dev, int wi
   if (st == TSDF_OK && e != cudaSuccess) st = tsdf::from_cuda(e);
 
   // the default (fused tile kernel) first, then every stage A x stage B
-  // pair, the fused warp kernel, and the other probe loads of the default
-  const Config dflt{1, 0, 2, 0, 0, 0};
+  // pair, the fused warp kernel, the other probe loads of the default, and
+  // the default with its walks split over 2, 4 and 8 threads per point
+  const Config dflt{1, 0, 2, 0, 0, 0, 1};
   std::vector<Config> cands{dflt};
   for (int a = 0; a <= 2; ++a)
-    for (int i = 0; i <= 1; ++i) cands.push_back({a, i, 0, 0, 0, 0});
-  cands.push_back({1, 0, 1, 0, 0, 0});
-  cands.push_back({1, 0, 2, 1, 0, 0});
-  cands.push_back({1, 0, 2, 2, 0, 0});
+    for (int i = 0; i <= 1; ++i) cands.push_back({a, i, 0, 0, 0, 0, 1});
+  cands.push_back({1, 0, 1, 0, 0, 0, 1});
+  cands.push_back({1, 0, 2, 1, 0, 0, 1});
+  cands.push_back({1, 0, 2, 2, 0, 0, 1});
+  if (vol->half_band == 2 || vol->half_band == 4 || vol->half_band == 8)
+    for (int t = 2; t <= 8; t *= 2) cands.push_back({1, 0, 2, 0, 0, 0, t});
 
   std::vector<float> times;
   for (size_t c = 0; c < cands.size() && st == TSDF_OK; ++c) {
@@ -207,7 +217,7 @@ tsdf_status tsdf_batch_autotune(tsdf_batch* batch, const tsdf_frame* frames, int
   };
 
   int tried = 0;
-  const Config dflt{1, 0, 2, 0, 0, 1};
+  const Config dflt{1, 0, 2, 0, 0, 1, 1};
   Config best = dflt;
   float best_ms = 0.0f, dflt_ms = 0.0f;
   if (st == TSDF_OK) st = run(dflt, &dflt_ms);
@@ -224,11 +234,11 @@ tsdf_status tsdf_batch_autotune(tsdf_batch* batch, const tsdf_frame* frames, int
     }
   };
   // stage 1: strategies (the batched kernels take stage A strategies 1 and 2)
-  consider({1, 0, 0, 0, 0, 1});
-  consider({1, 1, 0, 0, 0, 1});
-  consider({2, 0, 0, 0, 0, 1});
-  consider({2, 1, 0, 0, 0, 1});
-  consider({1, 0, 1, 0, 0, 1});
+  consider({1, 0, 0, 0, 0, 1, 1});
+  consider({1, 1, 0, 0, 0, 1, 1});
+  consider({2, 0, 0, 0, 0, 1, 1});
+  consider({2, 1, 0, 0, 0, 1, 1});
+  consider({1, 0, 1, 0, 0, 1, 1});
   // stage 2: resident CTAs per SM of the persistent grid
   const Config strat = best;
   for (int f = 1; f <= 4; ++f) {

@@ -34,6 +34,14 @@ def test_every_declared_symbol_is_exported(L):
     assert set(names) == set(tsdf.EXPORTED)
 
 
+def test_option_ids_match_the_header():
+    text = open(os.path.join(ROOT, "include", "tsdf.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    ids = {m.group(1).lower(): int(m.group(2))
+           for m in re.finditer(r"\bTSDF_OPT_([A-Z0-9_]+)\s*=\s*(\d+)", text)}
+    assert ids == tsdf.OPTIONS
+
+
 def test_packed_key_by_hand(L):
     b = 1 << 20
     assert tsdf.tsdf_block_key(0, 0, 0) == (b << 42) | (b << 21) | b

@@ -103,13 +103,30 @@ BANDS = [(0.05, 0.2), (0.1, 0.3), (0.03, 0.12), (0.02, 0.1), (0.04, 0.08), (0.01
 
 
 # (fuse, allocate, integrate) modes: the fused kernel, and the two-stage path
-# with each stage A and stage B strategy
+# with each stage A and stage B strategy; then the fused tile kernel with each
+# point's walk split over 2, 4 and 8 threads
 MODES = [dict(fuse_mode=2),
          dict(fuse_mode=1),
          dict(fuse_mode=0, allocate_mode=2, integrate_mode=1),
          dict(fuse_mode=0, allocate_mode=1, integrate_mode=1),
          dict(fuse_mode=0, allocate_mode=0, integrate_mode=0),
-         dict(fuse_mode=0, allocate_mode=1, integrate_mode=0)]
+         dict(fuse_mode=0, allocate_mode=1, integrate_mode=0),
+         dict(fuse_mode=2, threads_per_point=2),
+         dict(fuse_mode=2, threads_per_point=4),
+         dict(fuse_mode=2, threads_per_point=8)]
+SINGLE = [m for m in range(len(MODES)) if "threads_per_point" not in MODES[m]]
+SPLIT = [m for m in range(len(MODES)) if "threads_per_point" in MODES[m]]
+
+
+def half_band(v, tau):
+    return int(np.rint(np.float32(tau) / np.float32(v)))
+
+
+def allowed(mode, band=None, policy=0):
+    """The split walk exists for the default probe load and half bands 2, 4, 8."""
+    if mode in SINGLE:
+        return True
+    return policy == 0 and (band is None or half_band(*band) in (2, 4, 8))
 
 
 @pytest.mark.parametrize("seed", range(64))
@@ -117,16 +134,32 @@ def test_random_tiny_frames(seed):
     f = synth.random_frame(2000 + seed, width=16 + seed % 5, height=12 + seed % 3)
     v, tau = BANDS[seed % len(BANDS)]
     spec = synth.VolumeSpec(v, tau, 1 << 12, 1 << 12)
-    gv, ov = fuse_both([f], spec, **MODES[(seed // len(BANDS)) % len(MODES)])
+    gv, ov = fuse_both([f], spec, **MODES[SINGLE[(seed // len(BANDS)) % len(SINGLE)]])
     assert_same_volume(gv, ov)
 
 
-def test_ragged_tiles_and_odd_sizes():
-    """Image sizes that are not multiples of the 16x16 tile, down to 1x1."""
+SPLIT_BANDS = [b for b in BANDS if half_band(*b) in (2, 4, 8)]
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_random_tiny_frames_split_walk(seed):
+    """Random depth (holes, NaN, spikes) with the walk split over threads:
+    every span boundary of every half band, on ragged tiny frames."""
+    f = synth.random_frame(3000 + seed, width=13 + seed % 7, height=9 + seed % 4)
+    v, tau = SPLIT_BANDS[seed % len(SPLIT_BANDS)]
+    spec = synth.VolumeSpec(v, tau, 1 << 12, 1 << 12)
+    gv, ov = fuse_both([f], spec, **MODES[SPLIT[seed % len(SPLIT)]])
+    assert_same_volume(gv, ov)
+
+
+@pytest.mark.parametrize("mode", [SINGLE[0]] + SPLIT)
+def test_ragged_tiles_and_odd_sizes(mode):
+    """Image sizes that are not multiples of the tile (16x16, or 16 x 16/T
+    with T threads per point), down to 1x1."""
     for (w, h) in [(1, 1), (17, 3), (33, 31), (100, 7), (161, 121)]:
         f = synth.room_frame(5, width=w, height=h)
         spec = synth.VolumeSpec(0.02, 0.08, 1 << 14, 1 << 12)
-        gv, ov = fuse_both([f], spec)
+        gv, ov = fuse_both([f], spec, **MODES[mode])
         assert_same_volume(gv, ov)
 
 
@@ -154,8 +187,8 @@ def test_empty_and_invalid_frames():
 # ----------------------------------------------------------------------------
 # variants must not change the result
 # ----------------------------------------------------------------------------
-@pytest.mark.parametrize("mode", range(len(MODES)))
-@pytest.mark.parametrize("policy", [0, 1, 2])
+@pytest.mark.parametrize("policy,mode", [(p, m) for p in (0, 1, 2) for m in range(len(MODES))
+                                         if allowed(m, policy=p)])
 def test_probe_load_policies_and_modes(policy, mode):
     gv, ov = fuse_both([synth.room_frame(3, width=320, height=240)],
                        synth.VolumeSpec(0.005, 0.02, 1 << 16, 1 << 15), probe_load=policy,
@@ -163,8 +196,8 @@ def test_probe_load_policies_and_modes(policy, mode):
     assert_same_volume(gv, ov)
 
 
-@pytest.mark.parametrize("mode", range(len(MODES)))
-@pytest.mark.parametrize("band", BANDS)
+@pytest.mark.parametrize("band,mode", [(b, m) for b in BANDS for m in range(len(MODES))
+                                       if allowed(m, band=b)])
 def test_half_bands_on_room(band, mode):
     v, tau = band
     gv, ov = fuse_both([synth.room_frame(21, width=200, height=150)],
@@ -182,6 +215,30 @@ def test_room_640x480_every_mode(mode):
 def test_multi_frame_every_mode(mode):
     frames = [synth.room_frame(i * 11, width=320, height=240) for i in range(4)]
     gv, ov = fuse_both(frames, synth.VolumeSpec(0.005, 0.02, 1 << 18, 1 << 16), **MODES[mode])
+    assert_same_volume(gv, ov)
+
+
+def test_split_walk_option_rules():
+    v = gpu_volume(synth.VolumeSpec(0.01, 0.04, 1 << 12, 1 << 12))      # half band 4
+    for t in (0, 3, 16, -1):
+        assert v.set_option("threads_per_point", t) == "INVALID_ARG"
+    assert v.set_option("probe_load", 1) == "OK"
+    assert v.set_option("threads_per_point", 2) == "INVALID_ARG"       # default load only
+    assert v.set_option("probe_load", 0) == "OK"
+    assert v.set_option("threads_per_point", 4) == "OK"
+    assert v.set_option("probe_load", 2) == "INVALID_ARG"
+    assert v.set_option("threads_per_point", 1) == "OK"
+    assert v.set_option("probe_load", 2) == "OK"
+    m3 = gpu_volume(synth.VolumeSpec(0.1, 0.3, 1 << 12, 1 << 12))      # half band 3
+    assert m3.set_option("threads_per_point", 2) == "INVALID_ARG"
+    assert m3.set_option("threads_per_point", 1) == "OK"
+
+
+@pytest.mark.parametrize("fuse_mode", [0, 1])
+def test_split_walk_is_ignored_by_other_fuse_modes(fuse_mode):
+    f = synth.room_frame(9, width=160, height=120)
+    gv, ov = fuse_both([f], synth.VolumeSpec(0.01, 0.04, 1 << 14, 1 << 13),
+                       threads_per_point=8, fuse_mode=fuse_mode)
     assert_same_volume(gv, ov)
 
 
