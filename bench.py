@@ -687,6 +687,7 @@ def run_load_sweep(args, torch, tsdf, rendered):
     scrub = torch.ones(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     variants = (("fused_tile", work, snap, dict(fuse_mode=2)),
                 ("tile+scatter", work, snap, dict(allocate_mode=1, integrate_mode=0, fuse_mode=0)),
+                ("tile+tile", work, snap, dict(allocate_mode=1, integrate_mode=2, fuse_mode=0)),
                 ("paper_protocol", work, snap, dict(allocate_mode=0, integrate_mode=0, fuse_mode=0)),
                 ("fused_warp", work, snap, dict(fuse_mode=1)),
                 ("slot_index", kwork, ksnap, dict(fuse_mode=2)))

@@ -126,7 +126,11 @@ typedef enum tsdf_option {
    * reductions (a 16-byte vector of {tsdf, weight, red, green} and the blue
    * scalar), the paper's update stage (default); 1 = each warp dedupes its
    * points' blocks with __match_any_sync and looks them up once,
-   * warp-cooperatively, then the same additions. */
+   * warp-cooperatively, then the same additions; 2 = the distinct blocks of
+   * each 16x16 pixel tile are collected in shared memory and looked up once
+   * per tile, warp-cooperatively (long probe chains scanned by the whole
+   * warp), then the same additions with each index taken from the tile's
+   * list. Batches take 0 and 1. */
   TSDF_OPT_INTEGRATE_MODE = 2,
   /* Launch shape: threads per CTA for both stages (256). */
   TSDF_OPT_THREADS = 3,

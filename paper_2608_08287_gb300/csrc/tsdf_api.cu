@@ -276,7 +276,7 @@ tsdf_status tsdf_volume_set_option(tsdf_volume* vol, tsdf_option opt, int64_t va
       vol->va.timeout_ns = static_cast<unsigned long long>(value);
       return TSDF_OK;
     case TSDF_OPT_INTEGRATE_MODE:
-      if (value < 0 || value > 1) return TSDF_ERR_INVALID_ARG;
+      if (value < 0 || value > 2) return TSDF_ERR_INVALID_ARG;
       vol->integrate_mode = static_cast<int>(value);
       return TSDF_OK;
     case TSDF_OPT_THREADS:

@@ -811,4 +811,38 @@ __device__ __forceinline__ int resolve_for_update(const VolumeArgs& vol, int idx
   return -1;
 }
 
+// Stage B lookup, warp-cooperative (the tile strategy of stage B, after stage
+// A's kernel has completed): every lane with a key probes its own chain, one
+// slot per step, and chains still open after a few steps are fast-forwarded
+// by the whole warp (warp_skip_long_chains stops at the first slot holding
+// the key or empty, as the sequential probe would). Returns stage B's view:
+// the pool index, or -1 to skip the contribution (see resolve_for_update).
+template <int P>
+__device__ int warp_lookup_get(const VolumeArgs& vol, unsigned long long key, bool has) {
+  int bx = 0, by = 0, bz = 0;
+  if (has) unpack_key(key, bx, by, bz);
+  unsigned int s = has ? (hash_block(bx, by, bz) & vol.mask) : 0u;
+  bool todo = has;
+  unsigned int probe = 0, rounds = 0;
+  int result = kAbsent;
+  while (__any_sync(0xffffffffu, todo)) {
+    if (todo) {
+      unsigned long long k;
+      int idx;
+      load_entry<P>(vol.table + s, k, idx);
+      if (k == key) {
+        todo = false;
+        result = vol.slot_index ? static_cast<int>(s) : idx;
+      } else if (k == kEmptyKey) {
+        todo = false;
+      } else {
+        s = (s + 1) & vol.mask;
+        if (++probe >= vol.probe_limit) todo = false;
+      }
+    }
+    if (++rounds >= kCoopAfter) warp_skip_long_chains(vol, key, todo, s, probe);
+  }
+  return resolve_for_update(vol, result);
+}
+
 }  // namespace tsdf

@@ -19,15 +19,17 @@
 //     tile_allocate_kernel (phases 1 and 2 above, without waiting),
 //     warp_kernel<Allocate> (per warp, no shared memory);
 //   stage B: integrate_scatter_kernel (per-thread lookups, the paper's
-//     update), warp_kernel<Integrate> (warp-deduped lookups);
+//     update), warp_kernel<Integrate> (warp-deduped lookups), the tile kernel
+//     with phase 2 looking the tile's keys up warp-cooperatively;
 //   warp_kernel<Fused>: a barrier-free fused kernel, one warp per 8x4 patch.
 // Batched persistent variants serve many frames, each into its own volume,
 // per launch. Read-out, reset and diagnostics: export_kernel (means from
 // sums), slot_list_kernel, clear_used_kernel / clear_slots_kernel,
 // table_stats_kernel, weight_sum_kernel; surface extraction: extract_kernel.
 // The tile machinery and the tile kernels are in tsdf_tile.cuh; the fused
-// tile kernels with a point's walk split over several threads are compiled
-// in tsdf_kernels_split.cu.
+// tile kernels with a point's walk split over several threads, and the tile
+// kernel of stage B (tile_fused_kernel<..., kOpIntegrate>), are compiled in
+// tsdf_kernels_split.cu.
 
 #include <algorithm>
 #include <climits>
@@ -1056,8 +1058,10 @@ cudaError_t launch_integrate(const FrameArgs& f, const VolumeArgs& vol, int mode
       default: integrate_scatter_kernel<0><<<tiles, kThreads, 0, s>>>(f, vol, tx); break;
     }
     e = cudaGetLastError();
-  } else {
+  } else if (mode == 1) {
     e = launch_warp_m<kOpIntegrate, kLoadCached>(f, vol, s);
+  } else {
+    e = launch_integrate_tile(f, vol, s);
   }
   note_launch();
   return e;

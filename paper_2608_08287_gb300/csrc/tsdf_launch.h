@@ -13,6 +13,7 @@ void note_launch();
 
 cudaError_t launch_allocate(const FrameArgs& f, const VolumeArgs& vol, int probe_load, int mode,
                             cudaStream_t s);
+// Stage B: mode 0 = per-thread lookups, 1 = warp kernel, 2 = tile kernel.
 cudaError_t launch_integrate(const FrameArgs& f, const VolumeArgs& vol, int mode,
                              cudaStream_t s);
 // The fused path. threads_per_point > 1 (2, 4 or 8) takes the fused tile
@@ -21,6 +22,9 @@ cudaError_t launch_integrate(const FrameArgs& f, const VolumeArgs& vol, int mode
 // (cudaErrorInvalidValue otherwise).
 cudaError_t launch_fused(const FrameArgs& f, const VolumeArgs& vol, int probe_load, int mode,
                          int threads_per_point, cudaStream_t s);
+// Stage B, tile strategy (integrate mode 2): the fused tile kernel's phases
+// with phase 2 looking the tile's keys up instead of inserting them.
+cudaError_t launch_integrate_tile(const FrameArgs& f, const VolumeArgs& vol, cudaStream_t s);
 // The split-walk fused tile kernels (their own translation unit).
 cudaError_t launch_fused_split(const FrameArgs& f, const VolumeArgs& vol, int threads_per_point,
                                cudaStream_t s);

@@ -373,16 +373,20 @@ struct FusedTileShared {
   int idx[kTileList];
 };
 
+// Op: kOpFused (the fused path: phase 2 inserts and obtains the indices) or
+// kOpIntegrate (stage B of the two-stage path, after stage A's kernel: phase
+// 2 only looks the keys up, warp-cooperatively; the tile strategy of stage B).
 // TPP > 1 (threads per point, with the half band compiled): the TPP
 // consecutive threads of a point each walk a contiguous span of its 2M+1
 // samples, so a tile holds 256 / TPP points and a frame launches TPP times as
 // many CTAs -- more parallelism for small frames, at the price of one ray and
 // a two-sample lead-in per thread. Per voxel the arithmetic is unchanged.
-template <int P, int M, int TPP = 1>
+template <int P, int M, int TPP = 1, int Op = kOpFused>
 __device__ __forceinline__ void tile_fused_body(FusedTileShared& S, const FrameArgs& f,
                                                 const VolumeArgs& vol, int tile, int tiles_x) {
   static_assert(TPP == 1 || (M > 0 && (TPP & (TPP - 1)) == 0 && TPP <= 8),
                 "threads per point: 1, or 2, 4, 8 with the half band compiled");
+  static_assert(Op == kOpFused || Op == kOpIntegrate, "fused path or stage B");
   TileShared& T = S.T;
   tile_init(T, vol);
   __syncthreads();
@@ -424,26 +428,28 @@ __device__ __forceinline__ void tile_fused_body(FusedTileShared& S, const FrameA
     for (int k = 0; k < K; ++k) {
       const unsigned q = smp[k];
       if (q & kSampleValid)
-        point_key<kOpFused, P>(pk,
+        point_key<Op, P>(pk,
                                pack_key(bx0 + static_cast<int>((q >> 9) & 15u) - 8,
                                         by0 + static_cast<int>((q >> 13) & 15u) - 8,
                                         bz0 + static_cast<int>((q >> 17) & 15u) - 8),
                                T, vol);
     }
-    tile_list_point_keys<kOpFused, P>(T, vol, pk);
+    tile_list_point_keys<Op, P>(T, vol, pk);
   } else {
     Walk<M> w;
     unsigned acc;
-    tile_collect<kOpFused, P, M>(T, f, vol, r, valid, w, acc, pk);
+    tile_collect<Op, P, M>(T, f, vol, r, valid, w, acc, pk);
   }
   __syncthreads();
-  // phase 2: insert the list and obtain the indices
+  // phase 2: insert the list and obtain the indices (stage B: look them up)
   const int n = T.n < kTileList ? T.n : kTileList;
   const unsigned lane = threadIdx.x & 31u;
   for (int base = (threadIdx.x & ~31); base < n; base += blockDim.x) {
     const int i = base + static_cast<int>(lane);
     const bool has = i < n;
-    const int res = warp_insert_get<P>(vol, has ? T.list[i] : kEmptyKey, has);
+    const unsigned long long key = has ? T.list[i] : kEmptyKey;
+    const int res = Op == kOpFused ? warp_insert_get<P>(vol, key, has)
+                                   : warp_lookup_get<P>(vol, key, has);
     if (has) S.idx[i] = res;
   }
   __syncthreads();
@@ -461,7 +467,7 @@ __device__ __forceinline__ void tile_fused_body(FusedTileShared& S, const FrameA
   // a key missing from the list (set or list full) is resolved on its own
   auto index_of = [&](unsigned long long key) -> int {
     const int p = tile_find(T, key);
-    return p >= 0 ? S.idx[p] : resolve_single<kOpFused, P>(vol, key);
+    return p >= 0 ? S.idx[p] : resolve_single<Op, P>(vol, key);
   };
   BlockCacheT bc;
   if constexpr (M > 0) {
@@ -506,12 +512,12 @@ __device__ __forceinline__ void tile_fused_body(FusedTileShared& S, const FrameA
 // 64 registers a thread (four 256-thread CTAs per SM): the cap costs a few
 // spilled words in the walk and measured faster than three CTAs without
 // spills.
-template <int P, int M, int TPP = 1>
+template <int P, int M, int TPP = 1, int Op = kOpFused>
 __global__ void __launch_bounds__(kThreads, 4)
     tile_fused_kernel(const __grid_constant__ FrameArgs f, const __grid_constant__ VolumeArgs vol,
                       int tiles_x) {
   __shared__ FusedTileShared S;
-  tile_fused_body<P, M, TPP>(S, f, vol, blockIdx.x, tiles_x);
+  tile_fused_body<P, M, TPP, Op>(S, f, vol, blockIdx.x, tiles_x);
 }
 
 inline int tiles_of(int n) { return (n + kTile - 1) / kTile; }

@@ -134,7 +134,7 @@ tsdf_status tsdf_autotune_frame(tsdf_volume* vol, const float* depth_dev, int wi
   const Config dflt{1, 0, 2, 0, 0, 0, 1};
   std::vector<Config> cands{dflt};
   for (int a = 0; a <= 2; ++a)
-    for (int i = 0; i <= 1; ++i) cands.push_back({a, i, 0, 0, 0, 0, 1});
+    for (int i = 0; i <= 2; ++i) cands.push_back({a, i, 0, 0, 0, 0, 1});
   cands.push_back({1, 0, 1, 0, 0, 0, 1});
   cands.push_back({1, 0, 2, 1, 0, 0, 1});
   cands.push_back({1, 0, 2, 2, 0, 0, 1});

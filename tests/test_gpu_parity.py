@@ -103,7 +103,8 @@ BANDS = [(0.05, 0.2), (0.1, 0.3), (0.03, 0.12), (0.02, 0.1), (0.04, 0.08), (0.01
 
 
 # (fuse, allocate, integrate) modes: the fused kernel, and the two-stage path
-# with each stage A and stage B strategy; then the fused tile kernel with each
+# with each stage A and stage B strategy (stage B's tile strategy after both
+# the tile and the paper's stage A); then the fused tile kernel with each
 # point's walk split over 2, 4 and 8 threads
 MODES = [dict(fuse_mode=2),
          dict(fuse_mode=1),
@@ -111,6 +112,8 @@ MODES = [dict(fuse_mode=2),
          dict(fuse_mode=0, allocate_mode=1, integrate_mode=1),
          dict(fuse_mode=0, allocate_mode=0, integrate_mode=0),
          dict(fuse_mode=0, allocate_mode=1, integrate_mode=0),
+         dict(fuse_mode=0, allocate_mode=1, integrate_mode=2),
+         dict(fuse_mode=0, allocate_mode=0, integrate_mode=2),
          dict(fuse_mode=2, threads_per_point=2),
          dict(fuse_mode=2, threads_per_point=4),
          dict(fuse_mode=2, threads_per_point=8)]
