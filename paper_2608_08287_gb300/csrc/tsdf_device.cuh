@@ -221,9 +221,16 @@ __device__ __forceinline__ bool voxel_test(const FrameArgs& f, int gx, int gy, i
 // The band walk of one point with the half band M known at compile time: all
 // 2M+1 samples are unrolled, their depth gathers are issued together, and the
 // result is a mask of accepted samples (after the once-per-point dedupe of
-// voxels) with each sample's voxel and centre depth. Two samples are v apart
-// on a unit ray while a voxel's diagonal is v*sqrt(3) < 2v, so only the
-// previous two in-range samples can repeat a voxel.
+// voxels) with each sample's voxel and centre depth.
+//
+// The dedupe compares each sample with the previous one only. Every voxel
+// coordinate is a monotone function of k -- t_k = (k - M) v, the rounded
+// fused multiply-add t_k d + p, the product by 1/v and floor are each
+// monotone -- and so is the range test, so the in-range samples are
+// consecutive and a voxel equal to an earlier one is equal to all samples
+// between them, the previous sample included. "Not an earlier voxel of this
+// point" (Section 2.2) and "not the previous sample's voxel" are the same
+// test.
 template <int M>
 struct Walk {
   static constexpr int K = 2 * M + 1;
@@ -254,9 +261,6 @@ __device__ __forceinline__ unsigned walk_point(const FrameArgs& f, const Ray& r,
     if (k >= 1)
       fresh = fresh && !(((in_range >> (k - 1)) & 1u) && w.gx[k] == w.gx[k - 1] &&
                          w.gy[k] == w.gy[k - 1] && w.gz[k] == w.gz[k - 1]);
-    if (k >= 2)
-      fresh = fresh && !(((in_range >> (k - 2)) & 1u) && w.gx[k] == w.gx[k - 2] &&
-                         w.gy[k] == w.gy[k - 2] && w.gz[k] == w.gz[k - 2]);
     in_range |= ok ? (1u << k) : 0u;
     q[k] = fresh ? voxel_project(f, w.gx[k], w.gy[k], w.gz[k], w.zc[k]) : -1;
   }
@@ -323,12 +327,26 @@ __device__ __forceinline__ unsigned pack_sample(int dbx, int dby, int dbz, int l
          static_cast<unsigned>(l);
 }
 
+// The block offset fields of a packed sample (never all zero in a valid one:
+// each biased offset is at least 4).
+constexpr unsigned kSampleBlockBits = 0xFFFu << 9;
+
+// The key of a packed sample's block, given the block its offsets are from.
+__device__ __forceinline__ unsigned long long sample_key(unsigned q, int bx0, int by0, int bz0) {
+  return pack_key(bx0 + static_cast<int>((q >> 9) & 15u) - 8,
+                  by0 + static_cast<int>((q >> 13) & 15u) - 8,
+                  bz0 + static_cast<int>((q >> 17) & 15u) - 8);
+}
+
 // The band walk over samples lo .. lo+n-1 of one point (n <= C): the same
 // samples, dedupe and test as walk_point, each sample produced directly in
 // packed form. A rolling window of the two previous voxels replaces the
-// per-sample voxel arrays, so fewer registers are live at once; it starts two
-// samples before lo, so a walk split into spans over several threads dedupes
-// exactly as the whole walk does. Packing is relative to the block of the
+// per-sample voxel arrays, so few registers are live at once. (Comparing
+// with the previous voxel alone is the same test, see walk_point; with the
+// two-voxel window the fused tile kernel's registers are allocated without
+// spills, and it measured faster.) The window starts two samples before lo,
+// so a walk split into spans over several threads dedupes exactly as the
+// whole walk does. Packing is relative to the block of the
 // span's first in-range sample. Returns the mask of accepted samples (bit i
 // for sample lo+i); smp[i] and (with TSDF) tv[i] hold the packed voxel and the
 // tsdf value of each accepted one.
@@ -359,7 +377,7 @@ __device__ __forceinline__ unsigned walk_point_span(const FrameArgs& f, const Ra
                        !(c_ok && gx == cx && gy == cy && gz == cz);
     cx = ax; cy = ay; cz = az; c_ok = a_ok;
     ax = gx; ay = gy; az = gz; a_ok = ok;
-    if (i < 0) continue;  // the window's lead-in: voxel only
+    if (i < 0) continue;  // the sample before the span: voxel only
     if (ok && !have_base) {
       bx0 = gx >> 3;
       by0 = gy >> 3;

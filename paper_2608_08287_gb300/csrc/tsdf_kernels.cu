@@ -79,29 +79,31 @@ __device__ __forceinline__ void scatter_body(const FrameArgs& f, const VolumeArg
     cg = static_cast<float>(c[1]);
     cb = static_cast<float>(c[2]);
   }
-  BlockCacheT bc;
   if constexpr (M > 0) {
     unsigned smp[2 * M + 1];
     float tv[2 * M + 1];
     int bx0 = 0, by0 = 0, bz0 = 0;
     walk_point_packed<M>(f, r, smp, tv, bx0, by0, bz0);
+    unsigned last = 0u;  // block offset bits of the looked-up block (0: none yet)
+    int idx = -1;
 #pragma unroll
     for (int k = 0; k < 2 * M + 1; ++k) {
       const unsigned q = smp[k];
       if (!(q & kSampleValid)) continue;
-      const int bx = bx0 + static_cast<int>((q >> 9) & 15u) - 8;
-      const int by = by0 + static_cast<int>((q >> 13) & 15u) - 8;
-      const int bz = bz0 + static_cast<int>((q >> 17) & 15u) - 8;
-      const unsigned long long key = pack_key(bx, by, bz);
-      if (key != bc.key) {
-        bc.key = key;
-        bc.idx = resolve_for_update(vol, lookup_block(vol, key, bx, by, bz));
+      const unsigned blk = q & kSampleBlockBits;
+      if (blk != last) {
+        last = blk;
+        const int bx = bx0 + static_cast<int>((q >> 9) & 15u) - 8;
+        const int by = by0 + static_cast<int>((q >> 13) & 15u) - 8;
+        const int bz = bz0 + static_cast<int>((q >> 17) & 15u) - 8;
+        idx = resolve_for_update(vol, lookup_block(vol, pack_key(bx, by, bz), bx, by, bz));
       }
-      if (bc.idx >= 0)
-        add_contribution(vol.twrg, vol.blue, static_cast<size_t>(bc.idx) * kBlockVoxels + (q & 511u),
+      if (idx >= 0)
+        add_contribution(vol.twrg, vol.blue, static_cast<size_t>(idx) * kBlockVoxels + (q & 511u),
                          tv[k], colour, cr, cg, cb);
     }
   } else {
+    BlockCacheT bc;
     WalkDedupe walk;
     for (int k = 0; k <= 2 * f.M; ++k) {
       int gx, gy, gz;

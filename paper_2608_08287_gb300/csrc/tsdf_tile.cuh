@@ -424,15 +424,17 @@ __device__ __forceinline__ void tile_fused_body(FusedTileShared& S, const FrameA
         tv[k] = 0.0f;
       }
     }
+    // a sample's block offset is bits 9..20 of its packed word: the 64-bit
+    // key is built only where it changes
+    unsigned last = 0u;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       const unsigned q = smp[k];
-      if (q & kSampleValid)
-        point_key<Op, P>(pk,
-                               pack_key(bx0 + static_cast<int>((q >> 9) & 15u) - 8,
-                                        by0 + static_cast<int>((q >> 13) & 15u) - 8,
-                                        bz0 + static_cast<int>((q >> 17) & 15u) - 8),
-                               T, vol);
+      const unsigned blk = q & kSampleBlockBits;
+      if ((q & kSampleValid) && blk != last) {
+        last = blk;
+        point_key<Op, P>(pk, sample_key(q, bx0, by0, bz0), T, vol);
+      }
     }
     tile_list_point_keys<Op, P>(T, vol, pk);
   } else {
@@ -469,26 +471,25 @@ __device__ __forceinline__ void tile_fused_body(FusedTileShared& S, const FrameA
     const int p = tile_find(T, key);
     return p >= 0 ? S.idx[p] : resolve_single<Op, P>(vol, key);
   };
-  BlockCacheT bc;
   if constexpr (M > 0) {
+    unsigned last = 0u;  // block offset bits of the resolved block (0: none yet)
+    int idx = -1;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       const unsigned q = smp[k];
       if (!(q & kSampleValid)) continue;
-      const unsigned long long key =
-          pack_key(bx0 + static_cast<int>((q >> 9) & 15u) - 8,
-                   by0 + static_cast<int>((q >> 13) & 15u) - 8,
-                   bz0 + static_cast<int>((q >> 17) & 15u) - 8);
-      if (key != bc.key) {
-        bc.key = key;
-        bc.idx = index_of(key);
+      const unsigned blk = q & kSampleBlockBits;
+      if (blk != last) {
+        last = blk;
+        idx = index_of(sample_key(q, bx0, by0, bz0));
       }
-      if (bc.idx >= 0)
+      if (idx >= 0)
         add_contribution(vol.twrg, vol.blue,
-                         static_cast<size_t>(bc.idx) * kBlockVoxels + (q & 511u), tv[k], colour,
+                         static_cast<size_t>(idx) * kBlockVoxels + (q & 511u), tv[k], colour,
                          cr, cg, cb);
     }
   } else {
+    BlockCacheT bc;
     WalkDedupe walk;
     for (int k = 0; k <= 2 * f.M; ++k) {
       int gx, gy, gz;
