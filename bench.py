@@ -602,8 +602,9 @@ def run_small_frames(args, torch, tsdf):
     """Frames too small to fill the GPU with one thread per point: the
     160x120 plane-and-sphere frame (voxel 1 cm, truncation 4 cm, 2^16 slots,
     pool 2^14) and a 320x240 room frame (1 cm / 4 cm, 2^18 slots, pool 2^16),
-    each fused into an empty volume by the fused tile kernel with 1, 2, 4 and
-    8 threads per point, and what tsdf_autotune_frame picks. Device time per
+    each fused into an empty volume by the fused tile kernel with the threads
+    per point chosen per frame (the default) and set to 1, 2, 4 and 8, and
+    what tsdf_autotune_frame picks. Device time per
     step (CUDA events), L2 scrubbed and volume reset between steps."""
     from paper_2608_08287_gb300 import synth
     cases = [("plane_sphere_160x120", synth.plane_sphere_frame(), synth.PLANE_SPHERE_160),
@@ -621,7 +622,7 @@ def run_small_frames(args, torch, tsdf):
         intr, pose = tsdf.intrinsics(f.intr), tsdf.pose_struct(f.pose)
         vol = tsdf.Volume(spec.voxel_size, spec.truncation, spec.table_slots, spec.pool_blocks)
         row = {"points": int(f.valid_points)}
-        for tpp in (1, 2, 4, 8):
+        for tpp in (0, 1, 2, 4, 8):
             assert vol.set_option("threads_per_point", tpp) == "OK"
             ms = []
             for i in range(5 + steps):
@@ -638,9 +639,10 @@ def run_small_frames(args, torch, tsdf):
                     ms.append(e0.elapsed_time(e1))
             assert vol.status(sp) == "OK"
             med = float(np.median(ms))
-            row[f"tpp{tpp}_ms"] = round(med, 5)
-            row[f"tpp{tpp}_pts_per_s"] = round(f.valid_points / (med / 1e3), 1)
-        assert vol.set_option("threads_per_point", 1) == "OK"
+            name_t = f"tpp{tpp}" if tpp else "tpp_auto"
+            row[f"{name_t}_ms"] = round(med, 5)
+            row[f"{name_t}_pts_per_s"] = round(f.valid_points / (med / 1e3), 1)
+        assert vol.set_option("threads_per_point", 0) == "OK"
         assert vol.reset(sp) == "OK"
         st, tuning = vol.autotune(d, f.intr, f.pose, c, reps=10, stream=sp)
         assert st == "OK", st

@@ -181,14 +181,17 @@ typedef enum tsdf_option {
    * probe. Values above table_slots act as unbounded. */
   TSDF_OPT_PROBE_BOUND = 9,
   /* Threads per depth point in the fused tile kernel (TSDF_OPT_FUSE_MODE 2;
-   * other modes ignore it): 1 (default) = each thread walks its point's whole
-   * band; 2, 4 or 8 = the point's 2M+1 band samples are split into that many
+   * other modes ignore it): 1 = each thread walks its point's whole band;
+   * 2, 4 or 8 = the point's 2M+1 band samples are split into that many
    * contiguous spans, one per thread, so a frame runs on that many times more
-   * threads (for small frames that do not fill the GPU). The result is the
-   * same. Values above 1 need the default TSDF_OPT_PROBE_LOAD and a half band
-   * M = round(truncation / voxel_size) of 2, 4 or 8; TSDF_ERR_INVALID_ARG
-   * otherwise, and setting another probe load while it is above 1 is
-   * rejected too. Not a batch option. */
+   * threads (for small frames that do not fill the GPU); 0 (default) =
+   * chosen per frame: the largest of 1, 2 and 4 whose CTAs (one per
+   * 16 x 16/TPP pixels) fit the GPU at four per SM, where the split walk
+   * exists (default probe load, half band 2, 4 or 8), else 1. The result is
+   * the same for every value. Values above 1 need the default
+   * TSDF_OPT_PROBE_LOAD and a half band M = round(truncation / voxel_size)
+   * of 2, 4 or 8; TSDF_ERR_INVALID_ARG otherwise, and setting another probe
+   * load while it is above 1 is rejected too. Not a batch option. */
   TSDF_OPT_THREADS_PER_POINT = 10
 } tsdf_option;
 
@@ -360,7 +363,8 @@ typedef struct tsdf_tuning {
   int candidates;             /* configurations timed */
   float best_ms;              /* median time of the chosen configuration */
   float default_ms;           /* median time of the default configuration */
-  int threads_per_point;      /* volumes: the chosen TSDF_OPT_THREADS_PER_POINT (1 for a batch) */
+  int threads_per_point;      /* volumes: the chosen TSDF_OPT_THREADS_PER_POINT, 0 = automatic
+                                 (1 for a batch) */
 } tsdf_tuning;
 
 /* Tune `vol` for this frame: every stage A x stage B strategy, the fused

@@ -267,7 +267,7 @@ tsdf_status tsdf_volume_set_option(tsdf_volume* vol, tsdf_option opt, int64_t va
   switch (opt) {
     case TSDF_OPT_PROBE_LOAD:
       if (value < 0 || value > 2) return TSDF_ERR_INVALID_ARG;
-      if (value != tsdf::kLoadCached && vol->threads_per_point != 1)
+      if (value != tsdf::kLoadCached && vol->threads_per_point > 1)
         return TSDF_ERR_INVALID_ARG;  // the split walk exists for the default load only
       vol->probe_load = static_cast<int>(value);
       return TSDF_OK;
@@ -299,8 +299,9 @@ tsdf_status tsdf_volume_set_option(tsdf_volume* vol, tsdf_option opt, int64_t va
       vol->va.slot_index = static_cast<unsigned int>(value);
       return TSDF_OK;
     case TSDF_OPT_THREADS_PER_POINT:
-      if (value != 1 && value != 2 && value != 4 && value != 8) return TSDF_ERR_INVALID_ARG;
-      if (value != 1 && (vol->probe_load != tsdf::kLoadCached ||
+      if (value != 0 && value != 1 && value != 2 && value != 4 && value != 8)
+        return TSDF_ERR_INVALID_ARG;
+      if (value > 1 && (vol->probe_load != tsdf::kLoadCached ||
                          (vol->half_band != 2 && vol->half_band != 4 && vol->half_band != 8)))
         return TSDF_ERR_INVALID_ARG;
       vol->threads_per_point = static_cast<int>(value);
@@ -337,6 +338,29 @@ tsdf_status tsdf_volume_layout(const tsdf_volume* vol, tsdf_layout* out) {
   return TSDF_OK;
 }
 
+namespace {
+
+// Threads per point of the fused tile kernel for a width x height frame. An
+// explicit setting is taken as it is. Automatic (0): the largest of 1, 2, 4
+// whose CTAs (one per 16 x 16/TPP pixel tile) still fit the GPU's resident
+// slots at four CTAs per SM -- a frame that fills the GPU keeps one thread
+// per point -- where the split walk exists (fuse mode 2, the default probe
+// load, half band 2, 4 or 8), else 1.
+int threads_per_point(const tsdf_volume* vol, int width, int height) {
+  if (vol->fuse_mode != 2) return 1;
+  if (vol->threads_per_point != 0) return vol->threads_per_point;
+  if (vol->probe_load != tsdf::kLoadCached ||
+      (vol->half_band != 2 && vol->half_band != 4 && vol->half_band != 8))
+    return 1;
+  const long long tiles = static_cast<long long>((width + 15) / 16) * ((height + 15) / 16);
+  const long long slots = 4ll * (vol->sm_count > 0 ? vol->sm_count : 1);
+  int t = 1;
+  while (t < 4 && tiles * (2 * t) <= slots) t *= 2;
+  return t;
+}
+
+}  // namespace
+
 tsdf_status tsdf_allocate_async(tsdf_volume* vol, const float* depth_dev, int width,
                                 int height, const tsdf_intrinsics* intr,
                                 const tsdf_pose* pose, void* stream) {
@@ -370,9 +394,9 @@ tsdf_status tsdf_fuse_frame_async(tsdf_volume* vol, const float* depth_dev, int 
   if (vol->poisoned) return TSDF_ERR_POISONED;
   vol->dirty = true;
   if (vol->fuse_mode != 0)
-    return from_cuda(
-        tsdf::launch_fused(f, vol->va, vol->probe_load, vol->fuse_mode,
-                           vol->fuse_mode == 2 ? vol->threads_per_point : 1, as_stream(stream)));
+    return from_cuda(tsdf::launch_fused(f, vol->va, vol->probe_load, vol->fuse_mode,
+                                        threads_per_point(vol, width, height),
+                                        as_stream(stream)));
   cudaError_t e = tsdf::launch_allocate(f, vol->va, vol->probe_load, vol->allocate_mode,
                                         as_stream(stream));
   if (e == cudaSuccess) e = tsdf::launch_integrate(f, vol->va, vol->integrate_mode,

@@ -45,7 +45,7 @@ struct tsdf_volume {
   int allocate_mode = 1;
   int integrate_mode = 0;
   int fuse_mode = 2;
-  int threads_per_point = 1;  // of the fused tile kernel
+  int threads_per_point = 0;  // of the fused tile kernel (0: chosen per frame)
   int threads = 256;
   void* stage = nullptr;
   size_t stage_bytes = 0;

@@ -68,7 +68,7 @@ struct Events {
 };
 
 tsdf_status apply_volume(tsdf_volume* v, const Config& c) {
-  // one thread per point first: the probe load may only change then
+  // no split walk first: the probe load may only change then
   tsdf_status st = tsdf_volume_set_option(v, TSDF_OPT_THREADS_PER_POINT, 1);
   if (st == TSDF_OK) st = tsdf_volume_set_option(v, TSDF_OPT_ALLOCATE_MODE, c.allocate_mode);
   if (st == TSDF_OK) st = tsdf_volume_set_option(v, TSDF_OPT_INTEGRATE_MODE, c.integrate_mode);
@@ -128,16 +128,18 @@ tsdf_status tsdf_autotune_frame(tsdf_volume* vol, const float* depth_dev, int wi
   if (e == cudaSuccess) e = ev.init();
   if (st == TSDF_OK && e != cudaSuccess) st = tsdf::from_cuda(e);
 
-  // the default (fused tile kernel) first, then every stage A x stage B
-  // pair, the fused warp kernel, the other probe loads of the default, and
-  // the default with its walks split over 2, 4 and 8 threads per point
-  const Config dflt{1, 0, 2, 0, 0, 0, 1};
+  // the default (fused tile kernel, threads per point chosen per frame)
+  // first, then every stage A x stage B pair, the fused warp kernel, the
+  // other probe loads of the default, and the default with 1, 2, 4 and 8
+  // threads per point set explicitly
+  const Config dflt{1, 0, 2, 0, 0, 0, 0};
   std::vector<Config> cands{dflt};
   for (int a = 0; a <= 2; ++a)
     for (int i = 0; i <= 2; ++i) cands.push_back({a, i, 0, 0, 0, 0, 1});
   cands.push_back({1, 0, 1, 0, 0, 0, 1});
   cands.push_back({1, 0, 2, 1, 0, 0, 1});
   cands.push_back({1, 0, 2, 2, 0, 0, 1});
+  cands.push_back({1, 0, 2, 0, 0, 0, 1});
   if (vol->half_band == 2 || vol->half_band == 4 || vol->half_band == 8)
     for (int t = 2; t <= 8; t *= 2) cands.push_back({1, 0, 2, 0, 0, 0, t});
 

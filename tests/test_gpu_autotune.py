@@ -42,10 +42,10 @@ def check_tuning(t, batch):
         assert 0 <= t["ctas_per_sm"] <= 4 and t["use_graph"] in (0, 1)
         assert t["threads_per_point"] == 1
     else:
-        assert t["threads_per_point"] in (1, 2, 4, 8)
-        assert t["threads_per_point"] == 1 or (t["fuse_mode"] == 2 and t["probe_load"] == 0)
+        assert t["threads_per_point"] in (0, 1, 2, 4, 8)
+        assert t["threads_per_point"] <= 1 or (t["fuse_mode"] == 2 and t["probe_load"] == 0)
     assert 0 < t["best_ms"] <= t["default_ms"]
-    assert t["candidates"] >= (10 if batch else 16)
+    assert t["candidates"] >= (10 if batch else 17)
 
 
 def test_autotune_frame_keeps_the_volume_and_applies_the_choice():

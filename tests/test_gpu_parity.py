@@ -104,8 +104,9 @@ BANDS = [(0.05, 0.2), (0.1, 0.3), (0.03, 0.12), (0.02, 0.1), (0.04, 0.08), (0.01
 
 # (fuse, allocate, integrate) modes: the fused kernel, and the two-stage path
 # with each stage A and stage B strategy (stage B's tile strategy after both
-# the tile and the paper's stage A); then the fused tile kernel with each
-# point's walk split over 2, 4 and 8 threads
+# the tile and the paper's stage A); then the fused tile kernel with the
+# threads per point set explicitly to 1, 2, 4 and 8 (the default chooses
+# them per frame: 4 for the tiny and 160x120 frames, 1 at 640x480)
 MODES = [dict(fuse_mode=2),
          dict(fuse_mode=1),
          dict(fuse_mode=0, allocate_mode=2, integrate_mode=1),
@@ -114,11 +115,12 @@ MODES = [dict(fuse_mode=2),
          dict(fuse_mode=0, allocate_mode=1, integrate_mode=0),
          dict(fuse_mode=0, allocate_mode=1, integrate_mode=2),
          dict(fuse_mode=0, allocate_mode=0, integrate_mode=2),
+         dict(fuse_mode=2, threads_per_point=1),
          dict(fuse_mode=2, threads_per_point=2),
          dict(fuse_mode=2, threads_per_point=4),
          dict(fuse_mode=2, threads_per_point=8)]
-SINGLE = [m for m in range(len(MODES)) if "threads_per_point" not in MODES[m]]
-SPLIT = [m for m in range(len(MODES)) if "threads_per_point" in MODES[m]]
+SPLIT = [m for m in range(len(MODES)) if MODES[m].get("threads_per_point", 0) > 1]
+SINGLE = [m for m in range(len(MODES)) if m not in SPLIT]
 
 
 def half_band(v, tau):
@@ -223,10 +225,11 @@ def test_multi_frame_every_mode(mode):
 
 def test_split_walk_option_rules():
     v = gpu_volume(synth.VolumeSpec(0.01, 0.04, 1 << 12, 1 << 12))      # half band 4
-    for t in (0, 3, 16, -1):
+    for t in (3, 16, -1):
         assert v.set_option("threads_per_point", t) == "INVALID_ARG"
-    assert v.set_option("probe_load", 1) == "OK"
+    assert v.set_option("probe_load", 1) == "OK"                      # automatic: allowed
     assert v.set_option("threads_per_point", 2) == "INVALID_ARG"       # default load only
+    assert v.set_option("threads_per_point", 0) == "OK"
     assert v.set_option("probe_load", 0) == "OK"
     assert v.set_option("threads_per_point", 4) == "OK"
     assert v.set_option("probe_load", 2) == "INVALID_ARG"
@@ -235,6 +238,7 @@ def test_split_walk_option_rules():
     m3 = gpu_volume(synth.VolumeSpec(0.1, 0.3, 1 << 12, 1 << 12))      # half band 3
     assert m3.set_option("threads_per_point", 2) == "INVALID_ARG"
     assert m3.set_option("threads_per_point", 1) == "OK"
+    assert m3.set_option("threads_per_point", 0) == "OK"
 
 
 @pytest.mark.parametrize("fuse_mode", [0, 1])
