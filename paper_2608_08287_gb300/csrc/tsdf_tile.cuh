@@ -510,9 +510,9 @@ __device__ __forceinline__ void tile_fused_body(FusedTileShared& S, const FrameA
   }
 }
 
-// 64 registers a thread (four 256-thread CTAs per SM): the cap costs a few
-// spilled words in the walk and measured faster than three CTAs without
-// spills.
+// At most 64 registers a thread (four 256-thread CTAs per SM). The default
+// instantiation (half band 4, one thread per point) fits without spilling;
+// the cap measured faster than three CTAs per SM with more registers.
 template <int P, int M, int TPP = 1, int Op = kOpFused>
 __global__ void __launch_bounds__(kThreads, 4)
     tile_fused_kernel(const __grid_constant__ FrameArgs f, const __grid_constant__ VolumeArgs vol,
