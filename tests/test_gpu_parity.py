@@ -223,6 +223,48 @@ def test_multi_frame_every_mode(mode):
     assert_same_volume(gv, ov)
 
 
+def tie_frame(pose):
+    """Exact binary geometry: samples and projections land on voxel and pixel
+    boundaries (the oracle pins the same frame against the dense brute force)."""
+    H = W = 8
+    vals = (np.arange(H * W) % 13 + 20).astype(np.float32) / np.float32(16.0)
+    depth = vals.reshape(H, W)
+    depth[3, 3] = np.nextafter(depth[3, 3], np.float32(9))
+    depth[4, 5] = np.nextafter(depth[4, 5], np.float32(0))
+    return synth.Frame(depth=depth, rgb=np.full((H, W, 3), 100, np.uint8),
+                       intr=np.array([8.0, 8.0, 3.5, 3.5], dtype=np.float32),
+                       pose=pose.astype(np.float32))
+
+
+def ulp_frame():
+    """Depths one to three ulps either side of voxel boundaries (v = 1 cm)."""
+    H, W = 6, 7
+    d = np.empty(H * W, dtype=np.float32)
+    for i in range(H * W):
+        x = np.float32(1.23) + np.float32(0.01) * np.float32(i % 5)
+        for _ in range(i % 7 - 3):
+            x = np.nextafter(x, np.float32(9))
+        for _ in range(3 - i % 7):
+            x = np.nextafter(x, np.float32(0))
+        d[i] = x
+    return synth.Frame(depth=d.reshape(H, W), rgb=np.zeros((H, W, 3), np.uint8),
+                       intr=np.array([6.0, 6.0, 3.0, 2.5], np.float32),
+                       pose=np.eye(4, dtype=np.float32))
+
+
+@pytest.mark.parametrize("mode", range(len(MODES)))
+def test_floating_point_contract_on_boundaries(mode):
+    """The decisions that depend on floating point (voxel of a sample, pixel of
+    a centre, the occlusion test) on inputs built to sit on or within an ulp
+    of the boundaries: the block set and the weights are bit-exact."""
+    import math
+    turned = synth.make_pose(synth.rotation(math.pi / 2), [0.25, -0.5, 0.125])
+    for f, (v, tau) in ((tie_frame(np.eye(4)), (0.125, 0.5)), (tie_frame(turned), (0.125, 0.5)),
+                        (ulp_frame(), (0.01, 0.04))):
+        gv, ov = fuse_both([f], synth.VolumeSpec(v, tau, 1 << 14, 1 << 14), **MODES[mode])
+        assert assert_same_volume(gv, ov) > 0
+
+
 def test_split_walk_option_rules():
     v = gpu_volume(synth.VolumeSpec(0.01, 0.04, 1 << 12, 1 << 12))      # half band 4
     for t in (3, 16, -1):
