@@ -236,8 +236,9 @@ tsdf_status tsdf_volume_layout(const tsdf_volume* vol, tsdf_layout* out);
  * Fusion
  * ------------------------------------------------------------------------- */
 
-/* Fuse one frame: stage A then stage B, enqueued on `stream`, then wait for
- * the stream and return the volume's status (as tsdf_volume_status).
+/* Fuse one frame: stage A then stage B (by default both in one fused kernel,
+ * see TSDF_OPT_FUSE_MODE; the result is the same), enqueued on `stream`, then
+ * wait for the stream and return the volume's status (as tsdf_volume_status).
  * depth_dev: height*width float32, row-major, device memory; a pixel is valid
  *   iff finite and > 0. rgb_dev: height*width*3 uint8 (interleaved), device
  *   memory, or NULL to skip the colour sums. Both are only read, and only
