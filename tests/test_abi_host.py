@@ -97,6 +97,31 @@ def test_invalid_arguments_rejected_before_cuda(L):
     tsdf.tsdf_volume_destroy(None)
 
 
+def test_null_handles_rejected_before_cuda(L):
+    """Every entry point that takes a volume or batch refuses a null handle
+    with INVALID_ARG before any CUDA call (so this runs without a GPU)."""
+    eye = [1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1]
+    intr = (1, 1, 0, 0)
+    for name in tsdf.OPTIONS:
+        assert tsdf.tsdf_volume_set_option(None, name, 1) == "INVALID_ARG"
+        assert tsdf.tsdf_batch_set_option(None, name, 1) == "INVALID_ARG"
+    assert tsdf.tsdf_fuse_frame_async(None, 4096, 8, 8, intr, eye) == "INVALID_ARG"
+    assert tsdf.tsdf_fuse_frame_host(None, 4096, 8, 8, intr, eye) == "INVALID_ARG"
+    assert tsdf.tsdf_fuse_frame_host_noalloc(None, 4096, 8, 8, intr, eye) == "INVALID_ARG"
+    assert tsdf.tsdf_allocate_async(None, 4096, 8, 8, intr, eye) == "INVALID_ARG"
+    assert tsdf.tsdf_integrate_async(None, 4096, 8, 8, intr, eye) == "INVALID_ARG"
+    assert tsdf.tsdf_volume_copy(None, None) == "INVALID_ARG"
+    assert tsdf.tsdf_extract_mesh_async(None, None, None, 0, 4096) == "INVALID_ARG"
+    st, t = tsdf.tsdf_autotune_frame(None, 4096, 8, 8, intr, eye)
+    assert st == "INVALID_ARG" and t is None
+    for fn in (tsdf.tsdf_volume_block_count, tsdf.tsdf_export_blocks,
+               tsdf.tsdf_volume_table_stats):
+        with pytest.raises(tsdf.TsdfError) as e:
+            fn(None)
+        assert e.value.status == "INVALID_ARG"
+    assert tsdf.tsdf_launch_count() == 0          # nothing was launched
+
+
 def test_status_strings_and_version(L):
     for code, name in tsdf.STATUS.items():
         want = "TSDF_OK" if code == 0 else f"TSDF_ERR_{name}"
