@@ -8,7 +8,8 @@ mistakes are the kind a restatement of the paper could make -- a dropped
 term, a flipped sign, a transposed operand or index, a missing step -- in
 the fusion (Section 2.2 with reading R5: the half voxel of the centre map,
 the rotation of the point and of the ray, the occlusion test, the dedupe,
-the sample step, the local index) and in the extraction (readings E1-E4:
+the sample step, the local index, the colour channels) and in the extraction
+(readings E1-E4:
 the tetrahedra and their orientation, the case tables, the inside test, the
 vertex position, the unobserved-corner rule, the quad diagonal).
 
@@ -42,6 +43,8 @@ FUSION = {
     "no per-point dedupe": ("if (seen) continue;", ""),
     "projection drops cx": ("std::fmaf(fx, cc[0] * iz, cx)", "fx * (cc[0] * iz)"),
     "sample step 1.5 v": ("static_cast<float>(k - M) * v;", "static_cast<float>(k - M) * v * 1.5f;"),
+    "red and blue swapped": ("B.r_sum[l] += static_cast<double>(col[0]) / 255.0;",
+                             "B.r_sum[l] += static_cast<double>(col[2]) / 255.0;"),
 }
 
 EXTRACTION = {

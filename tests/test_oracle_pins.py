@@ -165,6 +165,41 @@ def test_plane_closed_form(pose_id):
     assert (want > 0.5).any() and (want < -0.5).any()
 
 
+def test_colour_means_closed_form():
+    """Reading R4: a voxel's colour is the mean over the points that reached it
+    of their own pixel's 8-bit colour, divided by 255. The left half of the
+    image is colour A, the right half colour B, so every voxel's mean is
+    A/255 + a (B - A)/255 with one mixing fraction a = n_B / w shared by the
+    three channels, n_B a whole number of points; voxels reached from one half
+    only carry exactly that colour."""
+    H, W, Z, split = 48, 64, np.float32(1.3), 35
+    A = np.array([10, 20, 30])
+    B = np.array([200, 150, 100])
+    rgb = np.empty((H, W, 3), np.uint8)
+    rgb[:, :split] = A
+    rgb[:, split:] = B
+    # about 4.6 pixels per 1 cm voxel, and a split inside a voxel: mixed voxels
+    fr = synth.Frame(depth=np.full((H, W), Z, np.float32), rgb=rgb,
+                     intr=np.array([600.0, 600.0, 31.5, 23.5], np.float32),
+                     pose=np.eye(4, dtype=np.float32))
+    ov, st = _fuse(fr, 0.01, 0.04)
+    assert st == "OK"
+    g, vals = voxel_arrays(*ov.export(double=True))
+    w = vals[:, 1]
+    col = vals[:, 2:5] * 255.0
+    alpha = (col - A) / (B - A)                      # per channel
+    assert np.allclose(alpha, alpha[:, :1], atol=1e-9)
+    nb = alpha[:, 0] * w
+    assert np.allclose(nb, np.round(nb), atol=1e-6)
+    assert np.all((np.round(nb) >= 0) & (np.round(nb) <= w))
+    pure_a, pure_b = np.isclose(alpha[:, 0], 0), np.isclose(alpha[:, 0], 1)
+    assert pure_a.sum() > 100 and pure_b.sum() > 100 and (~pure_a & ~pure_b).any()
+    # the pure voxels lie on their own side of the split, a voxel at most away
+    x_split = (split - 0.5 - 31.5) / 600.0 * 1.3
+    cx = (g[:, 0] + 0.5) * 0.01
+    assert np.all(cx[pure_a] < x_split + 0.01) and np.all(cx[pure_b] > x_split - 0.01)
+
+
 # ----------------------------------------------------------------------------
 # the paper's analytic gate: sphere within a quarter voxel
 # ----------------------------------------------------------------------------
