@@ -69,7 +69,7 @@ typedef enum tsdf_status {
   TSDF_ERR_POOL_FULL = 3,        /* more blocks than pool_blocks (Section 3.4) */
   TSDF_ERR_TABLE_FULL = 4,       /* a probe scanned every slot without room */
   TSDF_ERR_PUBLISH_TIMEOUT = 5,  /* a block index was never published */
-  TSDF_ERR_BOUNDS = 6,           /* an index check failed (defensive) */
+  TSDF_ERR_BOUNDS = 6,           /* reserved for bounds-checked kernels; never set now */
   TSDF_ERR_POISONED = 7,         /* volume holds an earlier error; reset it */
   TSDF_ERR_CUDA = 8              /* a CUDA runtime call failed */
 } tsdf_status;
