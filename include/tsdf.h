@@ -532,6 +532,31 @@ tsdf_status tsdf_volume_table_stats(tsdf_volume* vol, void* stream, tsdf_table_s
  * a fusion repeatedly from the same state). */
 tsdf_status tsdf_volume_copy(tsdf_volume* dst, const tsdf_volume* src, void* stream);
 
+/* Checkpoint and resume (not in the paper): a volume's whole state -- its
+ * device allocation, laid out as at the top of this header, and the poisoned
+ * flag -- in caller-owned host memory, behind a 64-byte header recording the
+ * voxel size, truncation, table_slots, pool_blocks and TSDF_OPT_SLOT_INDEX
+ * setting. tsdf_export_blocks returns means, which do not restore the sums
+ * bit for bit; a checkpoint does.
+ *
+ * tsdf_volume_checkpoint_bytes: the bytes a checkpoint of `vol` takes,
+ * 64 + tsdf_volume_bytes(table_slots, pool_blocks); 0 for NULL.
+ *
+ * tsdf_volume_save: write the checkpoint into `host` (at least that many
+ * bytes). The copy is ordered after the work already on `stream` and waited
+ * for, so `host` is complete on return. TSDF_ERR_INVALID_ARG for a NULL
+ * pointer, a short buffer, or a device other than the volume's current.
+ *
+ * tsdf_volume_load: replace the state of `vol` with a checkpoint. It must
+ * come from a volume with the same voxel size, truncation, table_slots,
+ * pool_blocks and slot-index setting, and be complete (TSDF_ERR_INVALID_ARG
+ * otherwise, also for a buffer that is not a checkpoint); nothing is changed
+ * then. Options other than the slot index are the volume's own. The copy is
+ * ordered on `stream` and waited for; `host` is only read during the call. */
+size_t tsdf_volume_checkpoint_bytes(const tsdf_volume* vol);
+tsdf_status tsdf_volume_save(const tsdf_volume* vol, void* host, size_t bytes, void* stream);
+tsdf_status tsdf_volume_load(tsdf_volume* vol, const void* host, size_t bytes, void* stream);
+
 /* ---------------------------------------------------------------------------
  * Exact integer helpers (the device code uses the same definitions)
  * ------------------------------------------------------------------------- */

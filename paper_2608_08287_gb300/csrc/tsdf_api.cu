@@ -185,6 +185,46 @@ tsdf_status make_frame(const tsdf_volume* v, const float* depth, int w, int h,
 
 using tsdf::make_frame;
 
+namespace {
+
+// Threads per point of the fused tile kernel for a width x height frame. An
+// explicit setting is taken as it is. Automatic (0): the largest of 1, 2, 4
+// whose CTAs (one per 16 x 16/TPP pixel tile) still fit the GPU's resident
+// slots at four CTAs per SM -- a frame that fills the GPU keeps one thread
+// per point -- where the split walk exists (fuse mode 2, the default probe
+// load, half band 2, 4 or 8), else 1.
+int threads_per_point(const tsdf_volume* vol, int width, int height) {
+  if (vol->fuse_mode != 2) return 1;
+  if (vol->threads_per_point != 0) return vol->threads_per_point;
+  if (vol->probe_load != tsdf::kLoadCached ||
+      (vol->half_band != 2 && vol->half_band != 4 && vol->half_band != 8))
+    return 1;
+  const long long tiles = static_cast<long long>((width + 15) / 16) * ((height + 15) / 16);
+  const long long slots = 4ll * (vol->sm_count > 0 ? vol->sm_count : 1);
+  int t = 1;
+  while (t < 4 && tiles * (2 * t) <= slots) t *= 2;
+  return t;
+}
+
+// Host-side header of a checkpoint, followed by the volume's whole device
+// allocation.
+struct CheckpointHeader {
+  char magic[8];
+  float voxel, trunc;
+  uint32_t slots, pool, slot_index, poisoned, dirty, pad;
+  uint64_t bytes;  // device bytes that follow
+  uint8_t reserved[16];
+};
+static_assert(sizeof(CheckpointHeader) == 64, "the checkpoint header is 64 bytes");
+constexpr char kCheckpointMagic[8] = {'T', 'S', 'D', 'F', 'C', 'K', 'P', '1'};
+
+bool on_volume_device(const tsdf_volume* vol) {
+  int dev = 0;
+  return cudaGetDevice(&dev) == cudaSuccess && dev == vol->device;
+}
+
+}  // namespace
+
 extern "C" {
 
 size_t tsdf_volume_bytes(uint32_t table_slots, uint32_t pool_blocks) {
@@ -337,29 +377,6 @@ tsdf_status tsdf_volume_layout(const tsdf_volume* vol, tsdf_layout* out) {
   out->coords_offset = vol->off.coords;
   return TSDF_OK;
 }
-
-namespace {
-
-// Threads per point of the fused tile kernel for a width x height frame. An
-// explicit setting is taken as it is. Automatic (0): the largest of 1, 2, 4
-// whose CTAs (one per 16 x 16/TPP pixel tile) still fit the GPU's resident
-// slots at four CTAs per SM -- a frame that fills the GPU keeps one thread
-// per point -- where the split walk exists (fuse mode 2, the default probe
-// load, half band 2, 4 or 8), else 1.
-int threads_per_point(const tsdf_volume* vol, int width, int height) {
-  if (vol->fuse_mode != 2) return 1;
-  if (vol->threads_per_point != 0) return vol->threads_per_point;
-  if (vol->probe_load != tsdf::kLoadCached ||
-      (vol->half_band != 2 && vol->half_band != 4 && vol->half_band != 8))
-    return 1;
-  const long long tiles = static_cast<long long>((width + 15) / 16) * ((height + 15) / 16);
-  const long long slots = 4ll * (vol->sm_count > 0 ? vol->sm_count : 1);
-  int t = 1;
-  while (t < 4 && tiles * (2 * t) <= slots) t *= 2;
-  return t;
-}
-
-}  // namespace
 
 tsdf_status tsdf_allocate_async(tsdf_volume* vol, const float* depth_dev, int width,
                                 int height, const tsdf_intrinsics* intr,
@@ -635,6 +652,53 @@ tsdf_status tsdf_volume_copy(tsdf_volume* dst, const tsdf_volume* src, void* str
   if (e != cudaSuccess) return from_cuda(e);
   dst->poisoned = src->poisoned;
   dst->dirty = src->dirty;
+  return TSDF_OK;
+}
+
+size_t tsdf_volume_checkpoint_bytes(const tsdf_volume* vol) {
+  return vol ? sizeof(CheckpointHeader) + vol->off.total : 0;
+}
+
+tsdf_status tsdf_volume_save(const tsdf_volume* vol, void* host, size_t bytes, void* stream) {
+  if (!vol || !host || bytes < tsdf_volume_checkpoint_bytes(vol)) return TSDF_ERR_INVALID_ARG;
+  if (!on_volume_device(vol)) return TSDF_ERR_INVALID_ARG;
+  CheckpointHeader h;
+  std::memset(&h, 0, sizeof(h));
+  std::memcpy(h.magic, kCheckpointMagic, sizeof(h.magic));
+  h.voxel = vol->voxel;
+  h.trunc = vol->trunc;
+  h.slots = vol->slots;
+  h.pool = vol->pool;
+  h.slot_index = vol->va.slot_index;
+  h.poisoned = vol->poisoned ? 1u : 0u;
+  h.dirty = vol->dirty ? 1u : 0u;
+  h.bytes = vol->off.total;
+  char* out = static_cast<char*>(host);
+  std::memcpy(out, &h, sizeof(h));
+  cudaStream_t s = as_stream(stream);
+  cudaError_t e = cudaMemcpyAsync(out + sizeof(h), vol->mem, vol->off.total,
+                                  cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return from_cuda(e);
+}
+
+tsdf_status tsdf_volume_load(tsdf_volume* vol, const void* host, size_t bytes, void* stream) {
+  if (!vol || !host || bytes < sizeof(CheckpointHeader)) return TSDF_ERR_INVALID_ARG;
+  CheckpointHeader h;
+  std::memcpy(&h, host, sizeof(h));
+  if (std::memcmp(h.magic, kCheckpointMagic, sizeof(h.magic)) != 0 || h.voxel != vol->voxel ||
+      h.trunc != vol->trunc || h.slots != vol->slots || h.pool != vol->pool ||
+      h.slot_index != vol->va.slot_index || h.bytes != vol->off.total ||
+      bytes < sizeof(h) + vol->off.total)
+    return TSDF_ERR_INVALID_ARG;
+  if (!on_volume_device(vol)) return TSDF_ERR_INVALID_ARG;
+  cudaStream_t s = as_stream(stream);
+  cudaError_t e = cudaMemcpyAsync(vol->mem, static_cast<const char*>(host) + sizeof(h),
+                                  vol->off.total, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return from_cuda(e);
+  vol->poisoned = h.poisoned != 0;
+  vol->dirty = h.dirty != 0;
   return TSDF_OK;
 }
 

@@ -41,7 +41,8 @@ EXPORTED = ("tsdf_volume_bytes", "tsdf_volume_create", "tsdf_volume_create_in",
             "tsdf_server_submit", "tsdf_server_poll", "tsdf_server_pending",
             "tsdf_server_replay", "tsdf_volume_table_stats", "tsdf_volume_copy",
             "tsdf_autotune_frame", "tsdf_batch_autotune", "tsdf_extract_mesh_async",
-            "tsdf_extract_mesh")
+            "tsdf_extract_mesh", "tsdf_volume_checkpoint_bytes", "tsdf_volume_save",
+            "tsdf_volume_load")
 
 
 class tsdf_intrinsics(ctypes.Structure):
@@ -176,6 +177,9 @@ def lib() -> ctypes.CDLL:
                                         ctypes.POINTER(tsdf_completion)]),
             "tsdf_volume_table_stats": (st, [_P, _P, ctypes.POINTER(tsdf_table_stats)]),
             "tsdf_volume_copy": (st, [_P, _P, _P]),
+            "tsdf_volume_checkpoint_bytes": (ctypes.c_size_t, [_P]),
+            "tsdf_volume_save": (st, [_P, _P, ctypes.c_size_t, _P]),
+            "tsdf_volume_load": (st, [_P, _P, ctypes.c_size_t, _P]),
             "tsdf_extract_mesh_async": (st, [_P, _P, _P, ctypes.c_uint32, _P, _P]),
             "tsdf_extract_mesh": (st, [_P, _P, _P, ctypes.c_uint32,
                                        ctypes.POINTER(ctypes.c_uint32),
@@ -387,6 +391,27 @@ def tsdf_volume_table_stats(vol, stream=None) -> dict:
 
 def tsdf_volume_copy(dst, src, stream=None) -> str:
     return _st(lib().tsdf_volume_copy(dst, src, _stream(stream)))
+
+
+def tsdf_volume_checkpoint_bytes(vol) -> int:
+    return int(lib().tsdf_volume_checkpoint_bytes(vol))
+
+
+def tsdf_volume_save(vol, stream=None):
+    """(status, the checkpoint as a uint8 numpy array, or None)."""
+    n = tsdf_volume_checkpoint_bytes(vol)
+    buf = np.empty(max(n, 1), dtype=np.uint8)
+    st = _st(lib().tsdf_volume_save(vol, buf.ctypes.data if n else None, n, _stream(stream)))
+    return st, (buf if st == "OK" else None)
+
+
+def tsdf_volume_load(vol, checkpoint, stream=None) -> str:
+    """checkpoint: a uint8 numpy array (or bytes) written by tsdf_volume_save."""
+    buf = np.ascontiguousarray(np.frombuffer(checkpoint, dtype=np.uint8)
+                               if isinstance(checkpoint, (bytes, bytearray)) else checkpoint,
+                               dtype=np.uint8)
+    return _st(lib().tsdf_volume_load(vol, buf.ctypes.data if buf.size else None, buf.size,
+                                      _stream(stream)))
 
 
 def tsdf_extract_mesh_async(vol, triangles, cells, capacity, count, stream=None) -> str:
@@ -658,3 +683,9 @@ class Volume:
 
     def copy_from(self, other, stream=None) -> str:
         return tsdf_volume_copy(self.handle, other.handle, stream)
+
+    def save(self, stream=None):
+        return tsdf_volume_save(self.handle, stream)
+
+    def load(self, checkpoint, stream=None) -> str:
+        return tsdf_volume_load(self.handle, checkpoint, stream)

@@ -6,6 +6,7 @@ CUDA call is exercised too."""
 import os
 import re
 
+import numpy as np
 import pytest
 
 from paper_2608_08287_gb300 import build as tb
@@ -119,6 +120,9 @@ def test_null_handles_rejected_before_cuda(L):
         with pytest.raises(tsdf.TsdfError) as e:
             fn(None)
         assert e.value.status == "INVALID_ARG"
+    assert tsdf.tsdf_volume_checkpoint_bytes(None) == 0
+    assert tsdf.tsdf_volume_save(None) == ("INVALID_ARG", None)
+    assert tsdf.tsdf_volume_load(None, np.zeros(64, np.uint8)) == "INVALID_ARG"
     assert tsdf.tsdf_launch_count() == 0          # nothing was launched
 
 
