@@ -281,8 +281,12 @@ tsdf_status tsdf_fuse_frame_host(tsdf_volume* vol, const float* depth_host, int 
  * call before any stream capture. Every call on a device shares the one array:
  * calls whose work overlaps on the GPU (two host threads, or two streams)
  * race on it and must be serialised by the caller. Each call waits for
- * `stream` before returning, so consecutive calls from one thread are safe.
- * The array keeps the last frame; each call overwrites what it reads. */
+ * `stream` before returning, on success and on every error after its copies
+ * are enqueued, so consecutive calls from one thread are safe. The frame is
+ * validated (as tsdf_fuse_frame does) before anything is copied. The array
+ * keeps the last frame; each call overwrites what it reads. The looked-up
+ * address is cached for the life of the CUDA context: cudaDeviceReset between
+ * calls is not supported. */
 tsdf_status tsdf_fuse_frame_host_noalloc(tsdf_volume* vol, const float* depth_host, int width,
                                          int height, const tsdf_intrinsics* intr,
                                          const tsdf_pose* pose, const uint8_t* rgb_host,

@@ -15,12 +15,15 @@
 // Every GPU that loads the library holds it until the process exits. Host code
 // cannot use the array's name as a device address, so the first call on each
 // device looks the address up with cudaGetSymbolAddress (with that device
-// current) and caches it; later calls reuse it.
+// current) and caches it; later calls reuse it. The cache lives as long as
+// the process's CUDA context: cudaDeviceReset is not supported between calls
+// (it would also destroy every volume).
 #include <mutex>
 
 #include <cuda_runtime.h>
 
 #include "tsdf.h"
+#include "tsdf_internal.h"
 
 namespace {
 
@@ -66,8 +69,15 @@ extern "C" tsdf_status tsdf_fuse_frame_host_noalloc(tsdf_volume* vol, const floa
     return TSDF_ERR_INVALID_ARG;
   const size_t npx = static_cast<size_t>(width) * static_cast<size_t>(height);
   if (npx > static_cast<size_t>(TSDF_NOALLOC_MAX_PIXELS)) return TSDF_ERR_INVALID_ARG;
+  // Every check the fuse call makes before it enqueues work is made here,
+  // before the staging copies: a call that is refused leaves no copy in
+  // flight into the shared array.
+  tsdf::FrameArgs f;
+  tsdf_status st = tsdf::make_frame(vol, depth_host, width, height, intr, pose, rgb_host, &f);
+  if (st != TSDF_OK) return st;
+  if (vol->poisoned) return TSDF_ERR_POISONED;
   void* base = nullptr;
-  const tsdf_status st = staging_address(&base);
+  st = staging_address(&base);
   if (st != TSDF_OK) return st;
   unsigned char* depth_dev = static_cast<unsigned char*>(base);
   unsigned char* rgb_dev = depth_dev + kDepthBytes;
@@ -78,10 +88,15 @@ extern "C" tsdf_status tsdf_fuse_frame_host_noalloc(tsdf_volume* vol, const floa
     e = cudaMemcpyAsync(rgb_dev, rgb_host, npx * 3, cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) {
     cudaGetLastError();
+    cudaStreamSynchronize(s);  // a first copy may be in flight
     return TSDF_ERR_CUDA;
   }
   // Both stages, then wait for the stream and read the status: the staging is
-  // free for the next call once this returns.
-  return tsdf_fuse_frame(vol, reinterpret_cast<const float*>(depth_dev), width, height, intr,
-                         pose, rgb_host ? rgb_dev : nullptr, stream);
+  // free for the next call once this returns. The fuse call synchronises the
+  // stream on success and on every device status; a launch that fails returns
+  // before that, so the copies are waited for here.
+  st = tsdf_fuse_frame(vol, reinterpret_cast<const float*>(depth_dev), width, height, intr,
+                       pose, rgb_host ? rgb_dev : nullptr, stream);
+  if (st != TSDF_OK) cudaStreamSynchronize(s);
+  return st;
 }
