@@ -357,6 +357,36 @@ tsdf_status tsdf_fuse_batch_async(tsdf_batch* batch, const tsdf_frame* frames, i
 tsdf_status tsdf_batch_status(tsdf_batch* batch, void* stream, tsdf_status* per_frame, int n);
 
 /* ---------------------------------------------------------------------------
+ * Streaming host input (not in the paper, whose harness fuses frames already
+ * in device memory, Section 4): a sequence of frames given in HOST memory,
+ * fused in order, each frame's host-to-device copy overlapping the fusion of
+ * the frame before it.
+ * ------------------------------------------------------------------------- */
+
+/* Fuse frames[0..n-1] in order, frames[i] into frames[i].volume (the same
+ * volume may take several frames, or each frame its own). Here depth and rgb
+ * are HOST pointers (height x width float32; height x width x 3 uint8 or
+ * NULL); in pinned memory the copies run asynchronously and overlap the
+ * kernels, otherwise they are staged by the CUDA runtime. Each frame is
+ * copied on a copy stream owned by frames[0].volume into one of its two
+ * staging slots (frame i into slot i mod 2, after the kernel of frame i-2 has
+ * finished reading it), then fused on `stream` exactly as
+ * tsdf_fuse_frame_async fuses it, and its volume's error word is copied back
+ * into pinned memory. The call waits once, for the whole sequence, then
+ * writes status[i] for every frame: OK, the frame's error (which poisons its
+ * volume), POISONED for a volume poisoned before the call or by an earlier
+ * frame of it. Returns the first non-OK status, else OK.
+ * Every frame is validated (as tsdf_fuse_frame does) before anything is
+ * enqueued; a frame that fails validation returns its error and enqueues
+ * nothing. The staging slots, the copy stream, its events and the pinned
+ * status words are made on the first call (or grown when a call needs larger
+ * slots or more frames) and kept until frames[0].volume is destroyed; a call
+ * on that volume must not overlap another such call. Host buffers may be
+ * reused when the call returns. The volumes must be on the current device. */
+tsdf_status tsdf_fuse_frames_host(const tsdf_frame* frames, int n, tsdf_status* status,
+                                  void* stream);
+
+/* ---------------------------------------------------------------------------
  * Autotuning (not in the paper): time the strategies on the caller's frames
  * and keep the fastest. Times are medians of `reps` repetitions (1..1000)
  * after one warm-up, CUDA events on `stream`, L2 evicted before each.

@@ -1,7 +1,7 @@
 """Build libtsdf.so in-tree with nvcc for sm_103a (GB300).
 
-The translation units (host runtime, batches, serving, tuning, and the
-kernels, split in two) compile in parallel, then link into
+The translation units (host runtime, batches, serving, streaming host input,
+tuning, and the kernels, split in two) compile in parallel, then link into
 ``paper_2608_08287_gb300/_build/libtsdf.so`` against the shared CUDA runtime
 (so the library and PyTorch share one runtime and one context).
 """
@@ -20,7 +20,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libtsdf.so")
 
 SOURCES = ("tsdf_api.cu", "tsdf_batch.cu", "tsdf_kernels.cu", "tsdf_kernels_split.cu",
-           "tsdf_noalloc.cu", "tsdf_serve.cu", "tsdf_tune.cu")
+           "tsdf_noalloc.cu", "tsdf_serve.cu", "tsdf_stream.cu", "tsdf_tune.cu")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # Host code is compiled with contraction off: the per-frame constants the
 # kernels' decisions depend on are computed in a fixed order of IEEE

@@ -298,6 +298,13 @@ void tsdf_volume_destroy(tsdf_volume* vol) {
   cudaDeviceSynchronize();
   if (vol->owns && vol->mem) cudaFree(vol->mem);
   if (vol->stage) cudaFree(vol->stage);
+  if (vol->stream_stage) cudaFree(vol->stream_stage);
+  if (vol->err_words) cudaFreeHost(vol->err_words);
+  for (int b = 0; b < 2; ++b) {
+    if (vol->ev_copied[b]) cudaEventDestroy(vol->ev_copied[b]);
+    if (vol->ev_free[b]) cudaEventDestroy(vol->ev_free[b]);
+  }
+  if (vol->copy_stream) cudaStreamDestroy(vol->copy_stream);
   if (vol->pinned) cudaFreeHost(vol->pinned);
   delete vol;
 }

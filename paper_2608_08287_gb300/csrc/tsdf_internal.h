@@ -49,6 +49,16 @@ struct tsdf_volume {
   int threads = 256;
   void* stage = nullptr;
   size_t stage_bytes = 0;
+  // streaming host input (tsdf_fuse_frames_host), made on first use: two
+  // staging slots, a copy stream, slot filled / slot free events, and pinned
+  // per-frame error words
+  void* stream_stage = nullptr;
+  size_t stream_slot_bytes = 0;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_copied[2] = {nullptr, nullptr};
+  cudaEvent_t ev_free[2] = {nullptr, nullptr};
+  uint32_t* err_words = nullptr;
+  int err_capacity = 0;
 };
 
 namespace tsdf {

@@ -22,7 +22,8 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OUT_OF_MEMORY", 3: "POOL_FULL", 4: "TAB
           5: "PUBLISH_TIMEOUT", 6: "BOUNDS", 7: "POISONED", 8: "CUDA"}
 OPTIONS = {"probe_load": 0, "publish_timeout_ns": 1, "integrate_mode": 2, "threads": 3,
            "allocate_mode": 4, "fuse_mode": 5, "ctas_per_sm": 6, "use_graph": 7,
-           "slot_index": 8, "probe_bound": 9, "threads_per_point": 10}
+           "slot_index": 8, "probe_bound": 9, "threads_per_point": 10,
+           "batch_stages": 11}
 ERRBITS = {"POOL_FULL": 1, "TABLE_FULL": 2, "PUBLISH_TIMEOUT": 4, "BOUNDS": 8}
 EMPTY_KEY = 0xFFFFFFFFFFFFFFFF
 NOALLOC_MAX_PIXELS = 1 << 20
@@ -31,7 +32,8 @@ CHANNELS = ("tsdf", "weight", "r", "g", "b")
 EXPORTED = ("tsdf_volume_bytes", "tsdf_volume_create", "tsdf_volume_create_in",
             "tsdf_volume_reset", "tsdf_volume_destroy", "tsdf_volume_set_option",
             "tsdf_volume_layout", "tsdf_fuse_frame", "tsdf_fuse_frame_async",
-            "tsdf_fuse_frame_host", "tsdf_fuse_frame_host_noalloc", "tsdf_allocate_async",
+            "tsdf_fuse_frame_host", "tsdf_fuse_frame_host_noalloc", "tsdf_fuse_frames_host",
+            "tsdf_allocate_async",
             "tsdf_integrate_async",
             "tsdf_volume_status", "tsdf_volume_block_count", "tsdf_export_blocks",
             "tsdf_block_key", "tsdf_block_slot", "tsdf_status_string", "tsdf_version",
@@ -42,7 +44,7 @@ EXPORTED = ("tsdf_volume_bytes", "tsdf_volume_create", "tsdf_volume_create_in",
             "tsdf_server_replay", "tsdf_volume_table_stats", "tsdf_volume_copy",
             "tsdf_autotune_frame", "tsdf_batch_autotune", "tsdf_extract_mesh_async",
             "tsdf_extract_mesh", "tsdf_volume_checkpoint_bytes", "tsdf_volume_save",
-            "tsdf_volume_load")
+            "tsdf_volume_load", "tsdf_set_l2_fetch_bytes")
 
 
 class tsdf_intrinsics(ctypes.Structure):
@@ -145,6 +147,8 @@ def lib() -> ctypes.CDLL:
             "tsdf_fuse_frame_host_noalloc": (st, [_P, _P, ctypes.c_int, ctypes.c_int,
                                                   ctypes.POINTER(tsdf_intrinsics),
                                                   ctypes.POINTER(tsdf_pose), _P, _P]),
+            "tsdf_fuse_frames_host": (st, [ctypes.POINTER(tsdf_frame), ctypes.c_int,
+                                           ctypes.POINTER(ctypes.c_int), _P]),
             "tsdf_allocate_async": (st, [_P, _P, ctypes.c_int, ctypes.c_int,
                                          ctypes.POINTER(tsdf_intrinsics),
                                          ctypes.POINTER(tsdf_pose), _P]),
@@ -160,6 +164,7 @@ def lib() -> ctypes.CDLL:
             "tsdf_status_string": (ctypes.c_char_p, [ctypes.c_int]),
             "tsdf_version": (ctypes.c_char_p, []),
             "tsdf_launch_count": (ctypes.c_uint64, []),
+            "tsdf_set_l2_fetch_bytes": (st, [ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
             "tsdf_batch_create": (st, [ctypes.c_int, ctypes.POINTER(_P)]),
             "tsdf_batch_destroy": (None, [_P]),
             "tsdf_batch_set_option": (st, [_P, ctypes.c_int, ctypes.c_int64]),
@@ -482,6 +487,13 @@ def tsdf_version() -> str:
     return lib().tsdf_version().decode()
 
 
+def tsdf_set_l2_fetch_bytes(nbytes):
+    """(status, the previous value) of the context-wide L2 fetch granularity."""
+    prev = ctypes.c_int(0)
+    st = _st(lib().tsdf_set_l2_fetch_bytes(int(nbytes), ctypes.byref(prev)))
+    return st, prev.value
+
+
 def tsdf_launch_count() -> int:
     return int(lib().tsdf_launch_count())
 
@@ -520,6 +532,30 @@ def make_frames(items):
         arr[i].intr = intrinsics(intr)
         arr[i].pose = pose_struct(pose)
     return arr
+
+
+def make_host_frames(items):
+    """ctypes array of tsdf_frame with HOST buffers, from (volume handle, depth,
+    rgb, intr, pose) tuples; depth and rgb are numpy arrays or CPU tensors
+    (rgb may be None)."""
+    arr = (tsdf_frame * len(items))()
+    for i, (vol, depth, rgb, intr, pose) in enumerate(items):
+        arr[i].volume = vol.value if isinstance(vol, ctypes.c_void_p) else vol
+        arr[i].depth = _hptr(depth)
+        arr[i].rgb = _hptr(rgb)
+        arr[i].height, arr[i].width = int(depth.shape[-2]), int(depth.shape[-1])
+        arr[i].intr = intrinsics(intr)
+        arr[i].pose = pose_struct(pose)
+    return arr
+
+
+def tsdf_fuse_frames_host(frames, n=None, stream=None):
+    """(status, [per-frame status]) for a ctypes array of tsdf_frame with host
+    buffers (make_host_frames)."""
+    n = len(frames) if n is None else n
+    out = (ctypes.c_int * max(1, n))()
+    st = _st(lib().tsdf_fuse_frames_host(frames, n, out, _stream(stream)))
+    return st, [_st(out[i]) for i in range(n)]
 
 
 def tsdf_fuse_batch_async(batch, frames, n=None, stream=None) -> str:
