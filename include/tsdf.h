@@ -192,7 +192,13 @@ typedef enum tsdf_option {
    * TSDF_OPT_PROBE_LOAD and a half band M = round(truncation / voxel_size)
    * of 2, 4 or 8; TSDF_ERR_INVALID_ARG otherwise, and setting another probe
    * load while it is above 1 is rejected too. Not a batch option. */
-  TSDF_OPT_THREADS_PER_POINT = 10
+  TSDF_OPT_THREADS_PER_POINT = 10,
+  /* Batches only, with TSDF_OPT_FUSE_MODE 0 (two stages): which stages a call
+   * launches. 3 = stage A then stage B (default); 1 = stage A alone; 2 =
+   * stage B alone, for frames whose stage A ran before (a separate call on
+   * the same frames) -- so that each stage can be timed on its own. Other
+   * fuse modes ignore it. */
+  TSDF_OPT_BATCH_STAGES = 11
 } tsdf_option;
 
 /* ---------------------------------------------------------------------------
@@ -609,6 +615,18 @@ const char* tsdf_status_string(tsdf_status s);
  * enqueued through the library (for accounting in benchmarks). */
 const char* tsdf_version(void);
 uint64_t tsdf_launch_count(void);
+
+/* Sets the largest number of bytes the L2 cache fetches from DRAM on a miss
+ * (CUDA's cudaLimitMaxL2FetchGranularity: 0, 32, 64 or 128) for the CUDA
+ * context of the current device, which this process shares with every other
+ * library in it; *previous (may be NULL) receives the value it replaces.
+ * Section 2.2's updates touch the five sums of scattered voxels: with 32, an
+ * L2 miss fetches only its own 32-byte sector, so the pool is read at sector
+ * granularity (no bytes fetched beside the touched sectors); the kernels'
+ * results do not depend on it. The limit lasts as long as the context, and
+ * is a hint the driver may round. Returns INVALID_ARG for other values,
+ * CUDA on a failed call. Not in the paper. */
+tsdf_status tsdf_set_l2_fetch_bytes(int bytes, int* previous);
 
 #ifdef __cplusplus
 }

@@ -736,4 +736,20 @@ const char* tsdf_version(void) { return "libtsdf 0.1 (sm_103a)"; }
 
 uint64_t tsdf_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
+tsdf_status tsdf_set_l2_fetch_bytes(int bytes, int* previous) {
+  if (bytes != 0 && bytes != 32 && bytes != 64 && bytes != 128) return TSDF_ERR_INVALID_ARG;
+  size_t cur = 0;
+  if (cudaDeviceGetLimit(&cur, cudaLimitMaxL2FetchGranularity) != cudaSuccess) {
+    cudaGetLastError();
+    return TSDF_ERR_CUDA;
+  }
+  if (cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, static_cast<size_t>(bytes)) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return TSDF_ERR_CUDA;
+  }
+  if (previous) *previous = static_cast<int>(cur);
+  return TSDF_OK;
+}
+
 }  // extern "C"

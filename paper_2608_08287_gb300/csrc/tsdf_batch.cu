@@ -38,6 +38,7 @@ struct tsdf_batch {
   unsigned* status_host = nullptr;
   // configuration
   int probe_load = 0, allocate_mode = 1, integrate_mode = 0, fuse_mode = 2, factor = 0;
+  int stages = 3;  // two-stage path: 1 = stage A, 2 = stage B, 3 = both
   int use_graph = 0;
   cudaStream_t capture = nullptr;
   cudaGraphExec_t exec[2] = {nullptr, nullptr};
@@ -47,8 +48,9 @@ struct tsdf_batch {
 namespace {
 
 long long config_key(const tsdf_batch* b, bool all_m4) {
-  return (((((static_cast<long long>(b->probe_load) * 4 + b->allocate_mode) * 4 +
-             b->integrate_mode) * 4 + b->fuse_mode) * 64) + b->factor) * 2 + (all_m4 ? 1 : 0);
+  return ((((((static_cast<long long>(b->probe_load) * 4 + b->allocate_mode) * 4 +
+              b->integrate_mode) * 4 + b->fuse_mode) * 64) + b->factor) * 4 + b->stages) * 2 +
+         (all_m4 ? 1 : 0);
 }
 
 void drop_graphs(tsdf_batch* b) {
@@ -66,7 +68,7 @@ cudaError_t enqueue(tsdf_batch* b, int slot, size_t bytes, int grid_limit, bool 
   if (e != cudaSuccess) return e;
   return tsdf::launch_batch(static_cast<const tsdf::BatchHeader*>(b->table_dev[slot]),
                             b->probe_load, b->allocate_mode, b->integrate_mode, b->fuse_mode,
-                            b->factor, grid_limit, all_m4, s);
+                            b->factor, grid_limit, all_m4, b->stages, s);
 }
 
 // A batch smaller than this many tiles is launched directly with a grid of its
@@ -148,6 +150,10 @@ tsdf_status tsdf_batch_set_option(tsdf_batch* b, tsdf_option opt, int64_t value)
     case TSDF_OPT_USE_GRAPH:
       if (value < 0 || value > 1) return TSDF_ERR_INVALID_ARG;
       b->use_graph = static_cast<int>(value);
+      return TSDF_OK;
+    case TSDF_OPT_BATCH_STAGES:
+      if (value < 1 || value > 3) return TSDF_ERR_INVALID_ARG;
+      b->stages = static_cast<int>(value);
       return TSDF_OK;
     default:
       return TSDF_ERR_INVALID_ARG;
@@ -231,7 +237,7 @@ tsdf_status tsdf_fuse_batch_async(tsdf_batch* b, const tsdf_frame* frames, int n
   if (e == cudaSuccess) e = cudaEventRecord(b->done[slot], s);
   if (e != cudaSuccess) return from_cuda(e);
   tsdf::note_launch();
-  if (b->fuse_mode == 0) tsdf::note_launch();
+  if (b->fuse_mode == 0 && b->stages == 3) tsdf::note_launch();
   b->used[slot] = true;
   return TSDF_OK;
 }

@@ -1154,8 +1154,8 @@ static cudaError_t launch_batch_fused(const BatchHeader* table, bool all_m4, int
 
 cudaError_t launch_batch(const BatchHeader* table, int probe_load, int allocate_mode,
                          int integrate_mode, int fuse_mode, int factor, int grid_limit,
-                         bool all_m4, cudaStream_t s) {
-  cudaError_t e;
+                         bool all_m4, int stages, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
   if (fuse_mode == 2) {
     switch (probe_load) {
       case kLoadL2: return launch_batch_fused<kLoadL2>(table, all_m4, factor, grid_limit, s);
@@ -1172,7 +1172,9 @@ cudaError_t launch_batch(const BatchHeader* table, int probe_load, int allocate_
         return launch_persistent(batch_point_kernel<kOpFused, kLoadCached>, table, factor, grid_limit, s);
     }
   }
-  if (allocate_mode == 2) {
+  if (!(stages & 1)) {
+    // stage B alone
+  } else if (allocate_mode == 2) {
     switch (probe_load) {
       case kLoadL2:
         e = launch_persistent(batch_point_kernel<kOpAllocate, kLoadL2>, table, factor, grid_limit, s);
@@ -1195,7 +1197,7 @@ cudaError_t launch_batch(const BatchHeader* table, int probe_load, int allocate_
         break;
     }
   }
-  if (e != cudaSuccess) return e;
+  if (e != cudaSuccess || !(stages & 2)) return e;
   if (integrate_mode == 1)
     return launch_persistent(batch_point_kernel<kOpIntegrate, kLoadCached>, table, factor, grid_limit, s);
   return launch_persistent(batch_point_kernel<kBatchScatter, kLoadCached>, table, factor, grid_limit, s);

@@ -32,9 +32,10 @@ cudaError_t launch_fused_split(const FrameArgs& f, const VolumeArgs& vol, int th
 // the fused kernel. factor caps the resident CTAs per SM (0 = as many as fit).
 // grid_limit > 0 caps the grid (e.g. at the batch's tile count). all_m4: every
 // frame has half band 4 (selects the fused kernel compiled for that band).
+// stages (fuse mode 0): 1 = stage A only, 2 = stage B only, 3 = both.
 cudaError_t launch_batch(const BatchHeader* table, int probe_load, int allocate_mode,
                          int integrate_mode, int fuse_mode, int factor, int grid_limit,
-                         bool all_m4, cudaStream_t s);
+                         bool all_m4, int stages, cudaStream_t s);
 cudaError_t launch_batch_status(const BatchHeader* table, unsigned* out, cudaStream_t s);
 // Means of n blocks into out (n x 5 x 512); block j is pool block list[j], or
 // j when list is null.
