@@ -49,13 +49,14 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def config_dict(spec, frames):
+def config_dict(spec, frames, l2_fetch_bytes=0):
     return {"workload": WORKLOAD, "width": 640, "height": 480,
             "voxel_m": spec.voxel_size, "truncation_m": spec.truncation,
             "table_slots": spec.table_slots, "pool_blocks": spec.pool_blocks,
             "points_per_frame": int(np.mean([f.valid_points for f in frames])),
             "distinct_frames": len(frames), "colour": True,
             "l2": "flushed between steps (512 MB write + 512 MB read, outside the timed events)",
+            "l2_fetch_bytes": l2_fetch_bytes or "context default",
             "volume": "reset between steps: every step fuses into an empty volume"}
 
 
@@ -198,6 +199,10 @@ def run_gpu(args, rank, world, local_rank):
         build_library()
     if world > 1:
         torch.distributed.barrier()
+    # the L2 fetch granularity (0: the CUDA context's default, unchanged)
+    if args.l2_fetch_bytes:
+        st, _ = tsdf.tsdf_set_l2_fetch_bytes(args.l2_fetch_bytes)
+        assert st == "OK", st
     spec = synth.ROOM_640
     frames = make_frames(rank)
     vol = tsdf.Volume(spec.voxel_size, spec.truncation, spec.table_slots, spec.pool_blocks)
@@ -213,14 +218,17 @@ def run_gpu(args, rank, world, local_rank):
     scrub = torch.ones(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     W, H = 640, 480
 
-    # per-frame work counts from the GPU result itself (fresh volume each time)
-    work = []
-    for f, (d, c) in zip(frames, dev):
+    # per-frame work counts (units of the algorithmic bytes) from the oracle,
+    # before any timing; the GPU's own export of each frame is compared with
+    # them as a cross-check
+    work = oracle_work_counts(frames, spec)
+    gpu_counts_match = True
+    for f, (d, c), w in zip(frames, dev, work):
         assert vol.reset(sp) == "OK"
         assert tsdf.tsdf_fuse_frame(vol.handle, d, W, H, f.intr, f.pose, c, sp) == "OK"
         coords, vox = vol.export(sp)
-        work.append({"points": f.valid_points, "blocks": len(coords),
-                     "voxels": int((vox[:, 1] > 0).sum())})
+        gpu_counts_match &= (len(coords) == w["blocks"] and
+                             int((vox[:, 1] > 0).sum()) == w["voxels"])
 
     def prepare(i):
         vol.reset(sp)
@@ -302,12 +310,12 @@ def run_gpu(args, rank, world, local_rank):
         except Exception as e:  # noqa: BLE001
             amortized = {"error": repr(e)}
 
-    # rooflines (Section 8(d) algorithmic bytes; work counts from the GPU's own export)
+    # rooflines: the algorithmic bytes of each stage from the oracle's work
+    # counts of the timed frames (every block is new: each step fuses into an
+    # empty volume, so N_new = U_b)
     hbm, peak_kind = peaks()
     mean = lambda k: float(np.mean([w[k] for w in work]))
-    a_bytes = 4 * W * H + 16 * mean("blocks") + 28 * mean("blocks")
-    b_bytes = 7 * W * H + 16 * mean("blocks") + 40 * mean("voxels")
-    f_bytes = 7 * W * H + 16 * mean("blocks") + 28 * mean("blocks") + 40 * mean("voxels")
+    a_bytes, b_bytes, f_bytes = (float(np.mean(x)) for x in zip(*[stage_bytes(w) for w in work]))
     a_ms, b_ms = float(np.mean(ta)), float(np.mean(tb_))
     step_mean = total_ms / args.steps
     a_gbs, b_gbs = a_bytes / (a_ms * 1e6), b_bytes / (b_ms * 1e6)
@@ -322,6 +330,8 @@ def run_gpu(args, rank, world, local_rank):
     roof = {"bound": "hbm", "kernel": dom[0], "achieved": round(dom[3], 1), "peak": hbm,
             "peak_kind": f"{peak_kind} hbm_gbs", "unit": "GB/s",
             "frac": round(dom[3] / hbm, 4), "algorithmic_bytes": int(dom[1]),
+            "work_counts": "oracle (U_b, N_new, U_v of each timed frame); the GPU export "
+                           + ("agrees" if gpu_counts_match else "DISAGREES"),
             "traffic": committed_traffic(dom[4])}
 
     # what the single-frame autotuner picks for this workload (a report: the
@@ -389,7 +399,7 @@ def run_gpu(args, rank, world, local_rank):
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(total_ms / args.steps, 5), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": config_dict(spec, frames),
+            "config": config_dict(spec, frames, args.l2_fetch_bytes),
             "stages": {"path": "fused kernel" if fused else "stage A + stage B",
                        "fused_hbm_frac": round(f_gbs / hbm, 4),
                        "split_allocate_ms": round(a_ms, 5), "split_integrate_ms": round(b_ms, 5),
@@ -520,21 +530,71 @@ def run_extraction_only(args):
     return {"extraction": out}
 
 
+E2E_STREAM = 16  # frames per streaming call, each into its own volume
+
+
 def run_e2e(args, vol, frames, torch, tsdf, sp, stream, flush, scrub, world=1):
-    """Same metric through tsdf_fuse_frame_host: pinned host depth + colour are
-    copied in, both stages run, the status word is read back, every step."""
+    """Same metric end to end through the public C ABI with host buffers.
+
+    Headline: tsdf_fuse_frames_host, the streaming call. Each call takes
+    E2E_STREAM frames from pinned host memory (the bench frames in turn), each
+    into its own freshly reset volume, as the device-timed steps do; inside
+    the call every frame's depth and colour are copied in (overlapping the
+    previous frame's kernel), fused, and its status word read back. Timed on
+    the host around each call; volumes reset and L2 scrubbed before each call,
+    outside the timing.
+    Also reported: tsdf_fuse_frame_host, one frame per call (copy in, fuse,
+    status read back, all in series)."""
+    from paper_2608_08287_gb300 import synth
+    spec = synth.ROOM_640
     host = [(torch.from_numpy(f.depth).pin_memory(), torch.from_numpy(f.rgb).pin_memory())
             for f in frames]
     W, H = 640, 480
-    for i in range(max(1, args.warmup)):
-        f = frames[i % len(frames)]
-        vol.reset(sp)
-        assert tsdf.tsdf_fuse_frame_host(vol.handle, host[i % len(frames)][0], W, H, f.intr,
-                                         f.pose, host[i % len(frames)][1], sp) == "OK"
+    structs = [(tsdf.intrinsics(f.intr), tsdf.pose_struct(f.pose)) for f in frames]
+    vols = [vol] + [tsdf.Volume(spec.voxel_size, spec.truncation, spec.table_slots,
+                                spec.pool_blocks) for _ in range(E2E_STREAM - 1)]
+    calls = max(1, args.steps // E2E_STREAM)
+
+    def items(c):
+        out = []
+        for j in range(E2E_STREAM):
+            i = (c * E2E_STREAM + j) % len(frames)
+            out.append((vols[j].handle, host[i][0], host[i][1], structs[i][0], structs[i][1]))
+        return out
+
+    arrays = [tsdf.make_host_frames(items(c)) for c in range(min(calls, len(frames)))]
+    for c in range(max(1, args.warmup)):
+        for v in vols:
+            v.reset(sp)
+        st, per = tsdf.tsdf_fuse_frames_host(arrays[c % len(arrays)], stream=sp)
+        assert st == "OK", per
     total = 0.0
     points = 0
-    structs = [(tsdf.intrinsics(f.intr), tsdf.pose_struct(f.pose)) for f in frames]
-    for i in range(args.steps):
+    for c in range(calls):
+        for v in vols:
+            v.reset(sp)
+        with torch.cuda.stream(stream):
+            l2_scrub(flush, scrub, c)
+        stream.synchronize()
+        t0 = time.perf_counter()
+        st, per = tsdf.tsdf_fuse_frames_host(arrays[c % len(arrays)], stream=sp)
+        total += time.perf_counter() - t0
+        assert st == "OK", per
+        points += sum(frames[(c * E2E_STREAM + j) % len(frames)].valid_points
+                      for j in range(E2E_STREAM))
+    for v in vols[1:]:
+        v.close()
+
+    # one frame per call, all in series
+    one_total = 0.0
+    one_points = 0
+    for i in range(max(1, args.warmup)):
+        vol.reset(sp)
+        assert tsdf.tsdf_fuse_frame_host(vol.handle, host[i % len(frames)][0], W, H,
+                                         structs[i % len(frames)][0],
+                                         structs[i % len(frames)][1],
+                                         host[i % len(frames)][1], sp) == "OK"
+    for i in range(min(args.steps, 100)):
         f = frames[i % len(frames)]
         d, c = host[i % len(frames)]
         intr, pose = structs[i % len(frames)]
@@ -544,13 +604,21 @@ def run_e2e(args, vol, frames, torch, tsdf, sp, stream, flush, scrub, world=1):
         stream.synchronize()
         t0 = time.perf_counter()
         st = tsdf.tsdf_fuse_frame_host(vol.handle, d, W, H, intr, pose, c, sp)
-        total += time.perf_counter() - t0
+        one_total += time.perf_counter() - t0
         assert st == "OK", st
-        points += f.valid_points
+        one_points += f.valid_points
     points, total = reduce_job(points, total, world, "cuda")
+    one_points, one_total = reduce_job(one_points, one_total, world, "cuda")
     return {"value": round(points / total, 1), "unit": UNIT,
-            "h2d_bytes_per_step": W * H * 4 + W * H * 3, "d2h_bytes_per_step": 8,
-            "call": "tsdf_fuse_frame_host (pinned host depth+rgb in, status word out)"}
+            "h2d_bytes_per_step": W * H * 4 + W * H * 3, "d2h_bytes_per_step": 4,
+            "call": f"tsdf_fuse_frames_host, {E2E_STREAM} frames per call from pinned host "
+                    "memory, each into its own reset volume; per frame: depth + colour in, "
+                    "status word out",
+            "l2": "scrubbed before each call; frames within a call run back to back",
+            "single_frame_call": {
+                "value": round(one_points / one_total, 1), "unit": UNIT,
+                "h2d_bytes_per_step": W * H * 4 + W * H * 3, "d2h_bytes_per_step": 8,
+                "call": "tsdf_fuse_frame_host (pinned host depth+rgb in, status words out)"}}
 
 
 def run_batched(args, torch, tsdf, serving, bank):
@@ -611,6 +679,54 @@ def run_batched(args, torch, tsdf, serving, bank):
     tp = timed(per_frame, args.batch_steps)
     for v in vols:
         assert v.status(sp_) == "OK"
+
+    # the two-stage batched path, each stage timed on its own: stage A (tile
+    # allocator) as one persistent launch over the 64 frames, then stage B
+    # (per-thread scatter) as another, each replayed from its own graph
+    batch_a = tsdf.Batch(n, use_graph=1, fuse_mode=0, allocate_mode=1, integrate_mode=0,
+                         batch_stages=1)
+    batch_b = tsdf.Batch(n, use_graph=1, fuse_mode=0, allocate_mode=1, integrate_mode=0,
+                         batch_stages=2)
+    ta_, tb_ = [], []
+    for i in range(3 + args.batch_steps):
+        prep(i)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record(stream)
+        assert batch_a.fuse_async(items, stream=sp_) == "OK"
+        ev[1].record(stream)
+        assert batch_b.fuse_async(items, stream=sp_) == "OK"
+        ev[2].record(stream)
+        stream.synchronize()
+        if i >= 3:
+            ta_.append(ev[0].elapsed_time(ev[1]))
+            tb_.append(ev[1].elapsed_time(ev[2]))
+    st, _ = batch_b.status(n, stream=sp_)
+    assert st == "OK", st
+    batch_a.close()
+    batch_b.close()
+    # algorithmic bytes of the batch from the oracle's work counts of its frames
+    wk = oracle_work_counts([(d.numpy(), c.numpy(), np.array([intr.fx, intr.fy, intr.cx, intr.cy],
+                                                              np.float32),
+                              np.array(pose.m, np.float32).reshape(4, 4),
+                              serving.SESSION_CLASSES[r])
+                             for (d, c, intr, pose, _), r in
+                             ((bank.get(r, i), r) for i, r in enumerate(res))], None)
+    sums = [sum(x) for x in zip(*[stage_bytes(w) for w in wk])]
+    hbm, peak_kind = peaks()
+    sa_ms, sb_ms = float(np.mean(ta_)), float(np.mean(tb_))
+    stage_rooflines = {
+        "peak_gbs": hbm, "peak_kind": f"{peak_kind} hbm_gbs",
+        "work_counts": "oracle, each frame into an empty volume",
+        "stage_a": {"kernel": "batch_tile_allocate_kernel", "ms": round(sa_ms, 4),
+                    "algorithmic_bytes": int(sums[0]),
+                    "frac": round(sums[0] / (sa_ms * 1e6) / hbm, 4)},
+        "stage_b": {"kernel": "batch_point_kernel (scatter)", "ms": round(sb_ms, 4),
+                    "algorithmic_bytes": int(sums[1]),
+                    "frac": round(sums[1] / (sb_ms * 1e6) / hbm, 4)},
+        "two_stage_pts_per_s": round(points / ((sa_ms + sb_ms) / 1e3), 1),
+        "fused": {"kernel": "batch_tile_fused_kernel", "ms": round(float(np.mean(tb)), 4),
+                  "algorithmic_bytes": int(sums[2]),
+                  "frac": round(sums[2] / (float(np.mean(tb)) * 1e6) / hbm, 4)}}
     # the batch autotuner on the same frames (volumes empty before and after)
     for v in vols:
         assert v.reset(sp_) == "OK"
@@ -629,7 +745,8 @@ def run_batched(args, torch, tsdf, serving, bank):
             "per_frame_ms_per_step": round(mp_, 4),
             "autotuned_pts_per_s": round(points / (mt / 1e3), 1),
             "autotuned_ms_per_step": round(mt, 4), "autotuned_config": tuning,
-            "launches_per_step": {"batched": 2, "per_frame": 2 * n},
+            "launches_per_step": {"batched": 1, "per_frame": n},
+            "stage_rooflines": stage_rooflines,
             "steps": args.batch_steps, "graph": True}
 
 
@@ -832,6 +949,148 @@ def run_load_sweep(args, torch, tsdf, rendered):
             "points": points}
 
 
+PROBE_CASE_LOADS = (0.1, 0.9)
+
+
+def run_probe_policy_case(args):
+    """The probe-load policy case (Section 6.2: whether a probe read is kept in
+    L1 decided speed there). The room orbit (640x480) is fused into a table
+    and pool of 2^17 blocks, with stage A and stage B as separate kernels of
+    the paper's own strategies (so no launch of the kernels below happens
+    while it fills). When the load first passes 0.1 and 0.9 the volume is
+    snapshotted. Then, at each load and for each probe-load policy (L1-cached,
+    L2-only, relaxed atomic), the next frame is fused from the snapshot by the
+    fused tile kernel, and allocated by the tile allocator of stage A: twelve
+    launches, each timed with CUDA events (median of --probe-case-reps, L2
+    scrubbed), in the order an ncu capture with -k and -c 12 sees them when
+    --probe-case-reps is 0 (one launch each, no scrub: ncu flushes the caches
+    itself). The snapshots are checkpoints in host memory, restored before
+    every launch, so the device holds a single volume."""
+    import multiprocessing as mp
+    import torch
+    from paper_2608_08287_gb300 import serving, synth, tsdf
+    from paper_2608_08287_gb300.build import build_library
+    build_library()
+    torch.cuda.set_device(0)
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        rendered = pool.starmap(serving._render, [(640, 480, k) for k in range(args.sweep_frames)])
+    spec = synth.VolumeSpec(0.005, 0.02, SWEEP_SLOTS, SWEEP_SLOTS)
+    stream = torch.cuda.Stream()
+    sp = stream.cuda_stream
+
+    def vol(**opts):
+        v = tsdf.Volume(spec.voxel_size, spec.truncation, spec.table_slots, spec.pool_blocks)
+        for k, x in opts.items():
+            assert v.set_option(k, x) == "OK"
+        return v
+
+    # snapshots are kept in host memory (checkpoints), so that the device holds
+    # one volume while the kernels below run (an ncu capture saves and
+    # restores device memory around its passes)
+    fill = vol(fuse_mode=0, allocate_mode=0, integrate_mode=0)
+    snaps = {}
+    targets = list(PROBE_CASE_LOADS)
+    for k, (d, c, intr, pose) in enumerate(rendered[:-1]):
+        dd, cc = torch.from_numpy(d).cuda(), torch.from_numpy(c).cuda()
+        assert tsdf.tsdf_fuse_frame(fill.handle, dd, 640, 480, intr, pose, cc, sp) == "OK"
+        n = fill.block_count(sp)
+        while targets and n >= targets[0] * SWEEP_SLOTS:
+            st_, snap = fill.save(sp)
+            assert st_ == "OK"
+            st = fill.table_stats(sp)
+            snaps[targets.pop(0)] = (snap, k + 1, {
+                "blocks": n, "load": round(n / SWEEP_SLOTS, 4),
+                "probe_mean": round(st["probe_sum"] / max(1, st["occupied_slots"]), 2),
+                "probe_max": st["probe_max"]})
+        if not targets:
+            break
+    fill.close()
+    del fill
+    torch.cuda.empty_cache()
+    work = vol()
+    flush = scrub = None
+    if args.probe_case_reps > 0:
+        flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+        scrub = torch.ones(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    out = {"workload": "room orbit 640x480, voxel 5 mm, truncation 2 cm, table 2^17 slots, "
+                       "pool 2^17 blocks; the next frame after each snapshot",
+           "policies": {"0": "ld.global.ca (L1-cached)", "1": "ld.global.cg (L2 only)",
+                        "2": "ld.relaxed.gpu (scoped atomic load)"},
+           "launch_order": "for each load: for each policy: fused tile kernel, then tile "
+                           "allocator", "loads": []}
+    for load in PROBE_CASE_LOADS:
+        if load not in snaps:
+            out["loads"].append({"target": load, "error": "not reached"})
+            continue
+        snap, nxt, info = snaps[load]
+        d, c, intr, pose = rendered[nxt]
+        dd, cc = torch.from_numpy(d).cuda(), torch.from_numpy(c).cuda()
+        row = dict(info, target=load, frame=nxt, policies={})
+        for policy in (0, 1, 2):
+            times = {}
+            for name, opts in (("fused_tile", dict(fuse_mode=2, probe_load=policy)),
+                               ("tile_allocate", dict(fuse_mode=0, allocate_mode=1,
+                                                      probe_load=policy))):
+                for k, x in opts.items():
+                    assert work.set_option(k, x) == "OK"
+                ts = []
+                for r in range(max(1, args.probe_case_reps)):
+                    assert work.load(snap, sp) == "OK"
+                    stream.synchronize()   # the restore's copy ends before the events
+                    if flush is not None:
+                        with torch.cuda.stream(stream):
+                            l2_scrub(flush, scrub, r)
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    if name == "fused_tile":
+                        assert tsdf.tsdf_fuse_frame_async(work.handle, dd, 640, 480, intr, pose,
+                                                          cc, sp) == "OK"
+                    else:
+                        assert tsdf.tsdf_allocate_async(work.handle, dd, 640, 480, intr, pose,
+                                                        sp) == "OK"
+                    e1.record(stream)
+                    stream.synchronize()
+                    assert work.status(sp) == "OK"
+                    ts.append(e0.elapsed_time(e1))
+                times[name + "_ms"] = round(float(np.median(ts)), 4)
+            row["policies"][str(policy)] = times
+        out["loads"].append(row)
+    return out
+
+
+def oracle_work_counts(frames, spec):
+    """The units of the algorithmic bytes for each frame, from the oracle:
+    valid points, distinct blocks (U_b), new blocks (N_new) and distinct
+    voxels (U_v), each frame fused into an empty volume (the CPU leg of the
+    bench; computed before any timing). frames: synth frames, or tuples
+    (depth, rgb, intr (4,), pose (4, 4), spec) each with its own volume spec."""
+    import oracle
+    out = []
+    for f in frames:
+        if isinstance(f, tuple):
+            depth, rgb, intr, pose, sp = f
+        else:
+            depth, rgb, intr, pose, sp = f.depth, f.rgb, f.intr, f.pose, spec
+        ov = oracle.OracleVolume(sp.voxel_size, sp.truncation, sp.table_slots, sp.pool_blocks)
+        assert ov.fuse(depth, intr, pose, rgb) == "OK"
+        st = ov.last_stats
+        ov.close()
+        out.append({"points": st["points"], "blocks": st["unique_blocks"],
+                    "new_blocks": st["new_blocks"], "voxels": st["unique_voxels"],
+                    "pixels": int(depth.shape[0] * depth.shape[1])})
+    return out
+
+
+def stage_bytes(w):
+    """Section 8(d) algorithmic bytes of one frame's stage A, stage B and both
+    stages fused, from its work counts (each frame into an empty volume)."""
+    a = 4 * w["pixels"] + 16 * w["blocks"] + 28 * w["new_blocks"]
+    b = 7 * w["pixels"] + 16 * w["blocks"] + 40 * w["voxels"]
+    f = 7 * w["pixels"] + 16 * w["blocks"] + 28 * w["new_blocks"] + 40 * w["voxels"]
+    return a, b, f
+
+
 def cpu_baseline(seconds):
     """The oracle as it stands, single-threaded on a host core, on whole frames."""
     import oracle
@@ -976,6 +1235,16 @@ def main():
     ap.add_argument("--sweep-frames", type=int, default=142,
                     help="orbit frames rendered for the load-factor sweep (0 = no sweep)")
     ap.add_argument("--sweep-reps", type=int, default=10)
+    ap.add_argument("--l2-fetch-bytes", type=int, default=0,
+                    help="set the context's L2 fetch granularity (32, 64, 128) through "
+                         "tsdf_set_l2_fetch_bytes before the run; 0 leaves the default")
+    ap.add_argument("--probe-policy-case", action="store_true",
+                    help="only the probe-load policy case: loads 0.1 and 0.9, three policies, "
+                         "the fused tile kernel and the stage A tile allocator (a small command "
+                         "for an ncu capture of the probe reads)")
+    ap.add_argument("--probe-case-reps", type=int, default=5,
+                    help="timed repetitions per launch of the probe-load policy case "
+                         "(0: one launch each and no L2 scrub, for an ncu capture)")
     ap.add_argument("--small-steps", type=int, default=100,
                     help="timed steps per threads-per-point setting on the small frames")
     args = ap.parse_args()
@@ -989,6 +1258,11 @@ def main():
     if args.impl == "reference":
         if rank == 0:
             print(json.dumps(run_reference(args)), flush=True)
+        return
+
+    if args.probe_policy_case:
+        if rank == 0:
+            print(json.dumps(run_probe_policy_case(args)), flush=True)
         return
 
     if args.extraction_only:
