@@ -178,6 +178,7 @@ tsdf_status make_frame(const tsdf_volume* v, const float* depth, int w, int h,
   f->neg_tau = -v->trunc;
   f->inv_tau = 1.0f / v->trunc;
   f->M = v->half_band;
+  f->err = &v->va.hdr->err;
   return TSDF_OK;
 }
 

@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include "tsdf.h"
+#include "tsdf_check.h"
 
 namespace tsdf {
 
@@ -79,6 +80,7 @@ struct FrameArgs {
   float v, inv_v;          // voxel size and its IEEE reciprocal
   float tau, neg_tau, inv_tau;
   int M;                   // half band, samples k = 0..2M
+  unsigned int* err;       // the volume's error word (range checks of image reads)
 };
 
 // Device view of one volume.
@@ -207,6 +209,31 @@ __device__ __forceinline__ int voxel_project(const FrameArgs& f, int gx, int gy,
   return static_cast<int>(qv) * f.W + static_cast<int>(qu);
 }
 
+// Depth at row-major pixel index q (checked builds: q inside the image, else
+// the BOUNDS bit and NaN, which no test accepts).
+__device__ __forceinline__ float load_depth(const FrameArgs& f, long long q) {
+  if (!index_ok_signed(q, static_cast<unsigned long long>(f.W) * static_cast<unsigned>(f.H),
+                       f.err))
+    return __int_as_float(0x7fc00000);
+  return __ldg(f.depth + q);
+}
+
+// Colour codes of pixel (u, v) (checked builds: inside the image, else the
+// BOUNDS bit and zeros).
+__device__ __forceinline__ void load_colour(const FrameArgs& f, int u, int v, float& cr, float& cg,
+                                            float& cb) {
+  const long long q = static_cast<long long>(v) * f.W + u;
+  if (!index_ok_signed(q, static_cast<unsigned long long>(f.W) * static_cast<unsigned>(f.H),
+                       f.err)) {
+    cr = cg = cb = 0.0f;
+    return;
+  }
+  const uint8_t* c = f.rgb + 3 * static_cast<size_t>(q);
+  cr = static_cast<float>(c[0]);
+  cg = static_cast<float>(c[1]);
+  cb = static_cast<float>(c[2]);
+}
+
 __device__ __forceinline__ bool voxel_accept(const FrameArgs& f, float d2, float zc) {
   return isfinite(d2) && d2 > 0.0f && __fsub_rn(d2, zc) >= f.neg_tau;
 }
@@ -215,7 +242,7 @@ __device__ __forceinline__ bool voxel_test(const FrameArgs& f, int gx, int gy, i
                                            float& zc) {
   const int q = voxel_project(f, gx, gy, gz, zc);
   if (q < 0) return false;
-  return voxel_accept(f, __ldg(f.depth + q), zc);
+  return voxel_accept(f, load_depth(f, q), zc);
 }
 
 // The band walk of one point with the half band M known at compile time: all
@@ -266,7 +293,7 @@ __device__ __forceinline__ unsigned walk_point(const FrameArgs& f, const Ray& r,
   }
   float d2[K];
 #pragma unroll
-  for (int k = 0; k < K; ++k) d2[k] = q[k] >= 0 ? __ldg(f.depth + q[k]) : 0.0f;
+  for (int k = 0; k < K; ++k) d2[k] = q[k] >= 0 ? load_depth(f, q[k]) : 0.0f;
   unsigned acc = 0;
 #pragma unroll
   for (int k = 0; k < K; ++k)
@@ -295,14 +322,17 @@ __device__ __forceinline__ void red_add_v2(float4* p, float a, float b) {
 
 // One contribution to voxel o of the pool (Section 2.2, "Update"): tsdf and a
 // weight of 1, and the point's colour when the frame has one -- five sums in
-// two fire-and-forget reductions (one 16-byte vector, one scalar).
-__device__ __forceinline__ void add_contribution(float4* twrg, float* blue, size_t o, float t,
+// two fire-and-forget reductions (one 16-byte vector, one scalar). Checked
+// builds: o inside the pool.
+__device__ __forceinline__ void add_contribution(const VolumeArgs& vol, size_t o, float t,
                                                  bool colour, float cr, float cg, float cb) {
+  if (!index_ok(o, static_cast<unsigned long long>(vol.pool) * kBlockVoxels, &vol.hdr->err))
+    return;
   if (colour) {
-    red_add_v4(twrg + o, t, 1.0f, cr, cg);
-    red_add(blue + o, cb);
+    red_add_v4(vol.twrg + o, t, 1.0f, cr, cg);
+    red_add(vol.blue + o, cb);
   } else {
-    red_add_v2(twrg + o, t, 1.0f);
+    red_add_v2(vol.twrg + o, t, 1.0f);
   }
 }
 
@@ -391,7 +421,7 @@ __device__ __forceinline__ unsigned walk_point_span(const FrameArgs& f, const Ra
   }
   float d2[C];
 #pragma unroll
-  for (int i = 0; i < C; ++i) d2[i] = q[i] >= 0 ? __ldg(f.depth + q[i]) : 0.0f;
+  for (int i = 0; i < C; ++i) d2[i] = q[i] >= 0 ? load_depth(f, q[i]) : 0.0f;
   unsigned acc = 0;
 #pragma unroll
   for (int i = 0; i < C; ++i) {
@@ -469,6 +499,23 @@ static __device__ __noinline__ int wait_published(const VolumeArgs& vol, const E
   return -1;
 }
 
+// Checked builds: slot s inside the table (else the BOUNDS bit, and the
+// caller ends its probe).
+__device__ __forceinline__ bool slot_ok(const VolumeArgs& vol, unsigned int s) {
+  return index_ok(s, vol.slots, &vol.hdr->err);
+}
+
+// Writes a new block's coordinates at pool index i (checked builds: i inside
+// the pool).
+__device__ __forceinline__ void store_coords(const VolumeArgs& vol, unsigned int i, int bx, int by,
+                                             int bz) {
+  if (!index_ok(i, vol.pool, &vol.hdr->err)) return;
+  int32_t* c = vol.coords + 3 * static_cast<size_t>(i);
+  c[0] = bx;
+  c[1] = by;
+  c[2] = bz;
+}
+
 __device__ __forceinline__ void red_add_u32(unsigned int* p, unsigned int v) {
   asm volatile("red.relaxed.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
@@ -500,6 +547,7 @@ __device__ int insert_block(const VolumeArgs& vol, unsigned long long key, int b
                             int bz) {
   unsigned int s = hash_block(bx, by, bz) & vol.mask;
   for (unsigned int probe = 0; probe < vol.probe_limit; ++probe, s = (s + 1) & vol.mask) {
+    if (!slot_ok(vol, s)) return -1;
     Entry* e = vol.table + s;
     unsigned long long k;
     int idx;
@@ -517,10 +565,7 @@ __device__ int insert_block(const VolumeArgs& vol, unsigned long long key, int b
           atomicExch(&e->idx, kFailedIdx);
           return -1;
         }
-        int32_t* c = vol.coords + 3 * static_cast<size_t>(i);
-        c[0] = bx;
-        c[1] = by;
-        c[2] = bz;
+        store_coords(vol, i, bx, by, bz);
         if (WAIT) __threadfence();  // coordinates visible before the index
         atomicExch(&e->idx, static_cast<int>(i));
         return static_cast<int>(i);
@@ -576,7 +621,7 @@ __device__ __forceinline__ void warp_skip_long_chains(const VolumeArgs& vol,
       const unsigned int left = vol.probe_limit - lprobe;
       const unsigned int window = left < 32u ? left : 32u;
       unsigned long long k = 0;
-      if (lane < window) {
+      if (lane < window && slot_ok(vol, (ls + lane) & vol.mask)) {
         asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];"
                      : "=l"(k)
                      : "l"(&vol.table[(ls + lane) & vol.mask].key)
@@ -628,6 +673,7 @@ __device__ void warp_insert_nowait(const VolumeArgs& vol, unsigned long long key
   unsigned int probe = 0, rounds = 0;
   while (__any_sync(0xffffffffu, todo)) {
     bool won = false;
+    if (todo && !slot_ok(vol, s)) todo = false;
     Entry* e = vol.table + s;
     if (todo) {
       unsigned long long k;
@@ -673,10 +719,7 @@ __device__ void warp_insert_nowait(const VolumeArgs& vol, unsigned long long key
           atomicOr(&vol.hdr->err, TSDF_ERRBIT_POOL_FULL);
           atomicExch(&e->idx, kFailedIdx);
         } else {
-          int32_t* c = vol.coords + 3 * static_cast<size_t>(i);
-          c[0] = bx;
-          c[1] = by;
-          c[2] = bz;
+          store_coords(vol, i, bx, by, bz);
           *reinterpret_cast<volatile int*>(&e->idx) = static_cast<int>(i);
         }
       }
@@ -702,6 +745,7 @@ __device__ int warp_insert_get(const VolumeArgs& vol, unsigned long long key, bo
   const Entry* hit = nullptr;
   while (__any_sync(0xffffffffu, todo)) {
     bool won = false;
+    if (todo && !slot_ok(vol, s)) todo = false;
     Entry* e = vol.table + s;
     if (todo) {
       unsigned long long k;
@@ -754,10 +798,7 @@ __device__ int warp_insert_get(const VolumeArgs& vol, unsigned long long key, bo
           atomicOr(&vol.hdr->err, TSDF_ERRBIT_POOL_FULL);
           atomicExch(&e->idx, kFailedIdx);
         } else {
-          int32_t* c = vol.coords + 3 * static_cast<size_t>(i);
-          c[0] = bx;
-          c[1] = by;
-          c[2] = bz;
+          store_coords(vol, i, bx, by, bz);
           // Readers in this pass use the index only to address the pool, never
           // the coordinates, so no fence is needed before publishing it, and
           // a plain store is enough (nothing reads the old value).
@@ -795,6 +836,9 @@ static __device__ __noinline__ int lookup_chain(const VolumeArgs& vol, unsigned 
                                                 unsigned int s) {
   const ulonglong2* t = reinterpret_cast<const ulonglong2*>(vol.table);
   for (unsigned int probe = 1; probe < vol.probe_limit; probe += 4, s = (s + 4) & vol.mask) {
+    if (!(slot_ok(vol, s) && slot_ok(vol, (s + 1) & vol.mask) && slot_ok(vol, (s + 2) & vol.mask) &&
+          slot_ok(vol, (s + 3) & vol.mask)))
+      return kAbsent;
     const ulonglong2 e0 = __ldg(t + s);
     const ulonglong2 e1 = __ldg(t + ((s + 1) & vol.mask));
     const ulonglong2 e2 = __ldg(t + ((s + 2) & vol.mask));
@@ -814,6 +858,7 @@ static __device__ __noinline__ int lookup_chain(const VolumeArgs& vol, unsigned 
 __device__ __forceinline__ int lookup_block(const VolumeArgs& vol, unsigned long long key, int bx,
                                             int by, int bz) {
   const unsigned int s = hash_block(bx, by, bz) & vol.mask;
+  if (!slot_ok(vol, s)) return kAbsent;
   const ulonglong2 ent = __ldg(reinterpret_cast<const ulonglong2*>(vol.table + s));
   if (ent.x == key) return found_index(vol, ent, s);
   if (ent.x == kEmptyKey || vol.probe_limit <= 1) return kAbsent;
@@ -844,6 +889,7 @@ __device__ int warp_lookup_get(const VolumeArgs& vol, unsigned long long key, bo
   unsigned int probe = 0, rounds = 0;
   int result = kAbsent;
   while (__any_sync(0xffffffffu, todo)) {
+    if (todo && !slot_ok(vol, s)) todo = false;
     if (todo) {
       unsigned long long k;
       int idx;

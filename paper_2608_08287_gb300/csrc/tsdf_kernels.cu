@@ -55,8 +55,7 @@ __device__ __forceinline__ void scatter_add(const FrameArgs& f, const VolumeArgs
     bc.idx = resolve_for_update(vol, lookup_block(vol, key, bx, by, bz));
   }
   if (bc.idx < 0) return;
-  add_contribution(vol.twrg, vol.blue,
-                   static_cast<size_t>(bc.idx) * kBlockVoxels + local_index(gx, gy, gz),
+  add_contribution(vol, static_cast<size_t>(bc.idx) * kBlockVoxels + local_index(gx, gy, gz),
                    tsdf_value(f, r.d, zc), colour, cr, cg, cb);
 }
 
@@ -70,14 +69,11 @@ __device__ __forceinline__ void scatter_body(const FrameArgs& f, const VolumeArg
   tile_pixel(tile, tiles_x, u, v);
   if (u >= f.W || v >= f.H) return;
   Ray r;
-  if (!make_ray(f, u, v, __ldg(f.depth + v * f.W + u), r)) return;
+  if (!make_ray(f, u, v, load_depth(f, static_cast<long long>(v) * f.W + u), r)) return;
   float cr = 0.0f, cg = 0.0f, cb = 0.0f;
   const bool colour = f.rgb != nullptr;
   if (colour) {
-    const uint8_t* c = f.rgb + 3 * (static_cast<size_t>(v) * f.W + u);
-    cr = static_cast<float>(c[0]);
-    cg = static_cast<float>(c[1]);
-    cb = static_cast<float>(c[2]);
+    load_colour(f, u, v, cr, cg, cb);
   }
   if constexpr (M > 0) {
     unsigned smp[2 * M + 1];
@@ -99,7 +95,7 @@ __device__ __forceinline__ void scatter_body(const FrameArgs& f, const VolumeArg
         idx = resolve_for_update(vol, lookup_block(vol, pack_key(bx, by, bz), bx, by, bz));
       }
       if (idx >= 0)
-        add_contribution(vol.twrg, vol.blue, static_cast<size_t>(idx) * kBlockVoxels + (q & 511u),
+        add_contribution(vol, static_cast<size_t>(idx) * kBlockVoxels + (q & 511u),
                          tv[k], colour, cr, cg, cb);
     }
   } else {
@@ -136,6 +132,8 @@ __global__ void export_kernel(const __grid_constant__ VolumeArgs vol, float* __r
     const size_t blk = j / kBlockVoxels;
     const size_t l = j % kBlockVoxels;
     const size_t i = (list ? static_cast<size_t>(list[blk]) : blk) * kBlockVoxels + l;
+    if (!index_ok(i, static_cast<unsigned long long>(vol.pool) * kBlockVoxels, &vol.hdr->err))
+      continue;
     const float4 s = vol.twrg[i];
     const float w = s.y;
     float* o = out + blk * 5 * kBlockVoxels + l;
@@ -471,7 +469,7 @@ __device__ __forceinline__ void stage_tile(const VolumeArgs& vol, const int* nb,
     if (h < kHalo) {
       const unsigned e = halo[h];
       const int idx = nb[(e >> 9) & 7u];
-      if (idx >= 0)
+      if (idx >= 0 && index_ok(idx, vol.pool, &vol.hdr->err))
         sum[j] = __ldg(reinterpret_cast<const float2*>(
             vol.twrg + static_cast<size_t>(idx) * kBlockVoxels + (e & 511u)));
     }
@@ -650,12 +648,7 @@ __device__ __noinline__ void extra_block_voxel(const FrameArgs& f, const VolumeA
   if (Op == kOpAllocate) return;
   const bool colour = f.rgb != nullptr;
   float cr = 0.0f, cg = 0.0f, cb = 0.0f;
-  if (colour) {
-    const uint8_t* c = f.rgb + 3 * (static_cast<size_t>(pv) * f.W + pu);
-    cr = c[0];
-    cg = c[1];
-    cb = c[2];
-  }
+  if (colour) load_colour(f, pu, pv, cr, cg, cb);
   add_voxel_direct(vol, idx, l, t, colour, cr, cg, cb);
 }
 
@@ -667,7 +660,8 @@ __device__ __forceinline__ void warp_body(const FrameArgs& f, const VolumeArgs& 
   int u, v;
   tile_pixel(tile, tiles_x, u, v);
   Ray r;
-  const bool valid = u < f.W && v < f.H && make_ray(f, u, v, __ldg(f.depth + v * f.W + u), r);
+  const bool valid =
+      u < f.W && v < f.H && make_ray(f, u, v, load_depth(f, static_cast<long long>(v) * f.W + u), r);
 
   // phase 1: walk; the point's first three distinct accepted blocks; every
   // accepted voxel packed as (local index, block slot) with its tsdf value
@@ -798,10 +792,7 @@ __device__ __forceinline__ void warp_body(const FrameArgs& f, const VolumeArgs& 
   float cr = 0.0f, cg = 0.0f, cb = 0.0f;
   const bool colour = f.rgb != nullptr;
   if (colour) {
-    const uint8_t* c = f.rgb + 3 * (static_cast<size_t>(v) * f.W + u);
-    cr = static_cast<float>(c[0]);
-    cg = static_cast<float>(c[1]);
-    cb = static_cast<float>(c[2]);
+    load_colour(f, u, v, cr, cg, cb);
   }
   if constexpr (M > 0) {
 #pragma unroll

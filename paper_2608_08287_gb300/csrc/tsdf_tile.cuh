@@ -72,7 +72,8 @@ __global__ void __launch_bounds__(kThreads)
   tile_pixel(blockIdx.x, tiles_x, u, v);
   Ray r;
   bool valid = false;
-  if (u < f.W && v < f.H) valid = make_ray(f, u, v, __ldg(f.depth + v * f.W + u), r);
+  if (u < f.W && v < f.H)
+    valid = make_ray(f, u, v, load_depth(f, static_cast<long long>(v) * f.W + u), r);
   const int lane = threadIdx.x & 31;
   unsigned long long last_key = kEmptyKey;
   WalkDedupe walk;
@@ -241,7 +242,7 @@ __device__ __forceinline__ bool tile_ray(const FrameArgs& f, int tile, int tiles
   else
     tile_pixel_shared<TPP>(tile, tiles_x, u, v);
   if (u >= f.W || v >= f.H) return false;
-  return make_ray(f, u, v, __ldg(f.depth + v * f.W + u), r);
+  return make_ray(f, u, v, load_depth(f, static_cast<long long>(v) * f.W + u), r);
 }
 
 // Pixel rows of one tile of a kernel whose points have TPP threads each.
@@ -314,7 +315,7 @@ __device__ __forceinline__ void tile_collect(TileShared& T, const FrameArgs& f,
 __device__ __forceinline__ void add_voxel_direct(const VolumeArgs& vol, int idx, int l, float t,
                                                  bool colour, float cr, float cg, float cb) {
   if (idx < 0) return;
-  add_contribution(vol.twrg, vol.blue, static_cast<size_t>(idx) * kBlockVoxels + l, t, colour,
+  add_contribution(vol, static_cast<size_t>(idx) * kBlockVoxels + l, t, colour,
                    cr, cg, cb);
 }
 
@@ -461,10 +462,7 @@ __device__ __forceinline__ void tile_fused_body(FusedTileShared& S, const FrameA
   float cr = 0.0f, cg = 0.0f, cb = 0.0f;
   const bool colour = f.rgb != nullptr;
   if (colour) {
-    const uint8_t* c = f.rgb + 3 * (static_cast<size_t>(v) * f.W + u);
-    cr = static_cast<float>(c[0]);
-    cg = static_cast<float>(c[1]);
-    cb = static_cast<float>(c[2]);
+    load_colour(f, u, v, cr, cg, cb);
   }
   // a key missing from the list (set or list full) is resolved on its own
   auto index_of = [&](unsigned long long key) -> int {
@@ -484,8 +482,7 @@ __device__ __forceinline__ void tile_fused_body(FusedTileShared& S, const FrameA
         idx = index_of(sample_key(q, bx0, by0, bz0));
       }
       if (idx >= 0)
-        add_contribution(vol.twrg, vol.blue,
-                         static_cast<size_t>(idx) * kBlockVoxels + (q & 511u), tv[k], colour,
+        add_contribution(vol, static_cast<size_t>(idx) * kBlockVoxels + (q & 511u), tv[k], colour,
                          cr, cg, cb);
     }
   } else {
@@ -503,8 +500,7 @@ __device__ __forceinline__ void tile_fused_body(FusedTileShared& S, const FrameA
         bc.idx = index_of(key);
       }
       if (bc.idx >= 0)
-        add_contribution(vol.twrg, vol.blue,
-                         static_cast<size_t>(bc.idx) * kBlockVoxels + local_index(gx, gy, gz),
+        add_contribution(vol, static_cast<size_t>(bc.idx) * kBlockVoxels + local_index(gx, gy, gz),
                          tsdf_value(f, r.d, zc), colour, cr, cg, cb);
     }
   }

@@ -7,7 +7,9 @@ handles (int) or None (the legacy default stream, which is PyTorch's default
 stream).
 
 The CUDA library must be built (``paper_2608_08287_gb300.build``); if it is
-missing, importing a function fails loudly -- there is no CPU fallback.
+missing, importing a function fails loudly -- there is no CPU fallback. With
+the environment variable TSDF_CHECKED=1 the checked build is loaded instead
+(every pool, table, coordinate and image index range-checked on the device).
 """
 from __future__ import annotations
 
@@ -16,7 +18,7 @@ import os
 
 import numpy as np
 
-from .build import LIB
+from .build import LIB, LIB_CHECKED
 
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OUT_OF_MEMORY", 3: "POOL_FULL", 4: "TABLE_FULL",
           5: "PUBLISH_TIMEOUT", 6: "BOUNDS", 7: "POISONED", 8: "CUDA"}
@@ -118,11 +120,12 @@ def lib() -> ctypes.CDLL:
     """The loaded libtsdf.so; raises if it has not been built."""
     global _lib
     if _lib is None:
-        if not os.path.exists(LIB):
+        path = LIB_CHECKED if os.environ.get("TSDF_CHECKED") == "1" else LIB
+        if not os.path.exists(path):
             raise RuntimeError(
-                f"libtsdf.so is not built ({LIB}); run "
+                f"libtsdf.so is not built ({path}); run "
                 "`python -c 'import __graft_entry__ as g; g.build()'` first")
-        L = ctypes.CDLL(LIB)
+        L = ctypes.CDLL(path)
         st = ctypes.c_int
         sig = {
             "tsdf_volume_bytes": (ctypes.c_size_t, [ctypes.c_uint32, ctypes.c_uint32]),

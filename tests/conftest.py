@@ -14,3 +14,8 @@ if HERE not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
     config.addinivalue_line("markers", "slow: long-running case")
+    if os.environ.get("TSDF_CHECKED") == "1":
+        # the suite runs against the checked library (range checks on every
+        # device index): make sure it is built
+        from paper_2608_08287_gb300.build import build_library
+        build_library(checked=True)
