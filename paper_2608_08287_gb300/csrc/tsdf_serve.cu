@@ -4,11 +4,16 @@
 // tagged with their arrival time; tsdf_server_poll drives the loop:
 //   1. every launch whose completion event has fired is retired: its frames
 //      get their completion time, their staging slots are freed;
-//   2. while fewer than max_inflight launches are in flight, the frames at the
+//   2. (mode 0) the head frame of every session is copied into device staging
+//      as soon as a staging slot is free, on a copy stream of its own, so
+//      that frames queued behind a running launch are on the device when
+//      their turn comes;
+//   3. while fewer than max_inflight launches are in flight, the frames at the
 //      head of every session that has none in flight (oldest arrival first,
-//      at most max_batch) are copied into device staging and launched --
-//      as one batched fusion (mode 0; a batch of one frame takes the
-//      single-frame path), or one frame per launch (mode 1, the baseline).
+//      at most max_batch) are launched -- as one batched fusion (mode 0; a
+//      batch of one frame takes the single-frame path, and the launch waits
+//      for the frames' copies), or one frame per launch with its copy just
+//      before it on the same stream (mode 1, the baseline).
 // Each session's frames therefore run in arrival order (one stream, at most
 // one frame of a session per launch), frames that arrive while others run join
 // the next launch, and nothing is allocated after creation.
@@ -37,6 +42,7 @@ struct Pending {
   double arrival;
   uint64_t tag;
   int reset;  // empty the volume before fusing this frame
+  int slot = -1;  // staging slot once its copy is enqueued (mode 0), else -1
 };
 
 struct InFlight {
@@ -56,6 +62,8 @@ struct tsdf_server {
   std::vector<int> free_slots;
   tsdf_batch* batch = nullptr;
   cudaStream_t stream = nullptr;
+  cudaStream_t copy_stream = nullptr;      // mode 0: the eager copies
+  std::vector<cudaEvent_t> slot_copied;    // mode 0: per staging slot, its copy done
   std::unordered_map<tsdf_volume*, std::deque<Pending>> queues;
   std::unordered_map<tsdf_volume*, int> busy;
   std::deque<InFlight> inflight;
@@ -72,6 +80,33 @@ double now_s(const tsdf_server* s) {
   return std::chrono::duration<double>(std::chrono::steady_clock::now() - s->t0).count();
 }
 
+// Copy a frame into staging slot `slot` on stream cs.
+void copy_in(tsdf_server* s, const Pending& p, int slot, cudaStream_t cs) {
+  char* dst = s->staging + static_cast<size_t>(slot) * s->slot_bytes;
+  const size_t npx = static_cast<size_t>(p.w) * p.h;
+  const size_t dbytes = tsdf::align_up(npx * sizeof(float));
+  cudaMemcpyAsync(dst, p.depth, npx * sizeof(float), cudaMemcpyHostToDevice, cs);
+  if (p.rgb) cudaMemcpyAsync(dst + dbytes, p.rgb, npx * 3, cudaMemcpyHostToDevice, cs);
+}
+
+// Mode 0: give every session's head frame a staging slot and enqueue its copy
+// on the copy stream (oldest arrival first, while slots last).
+void copy_heads(tsdf_server* s) {
+  std::vector<std::pair<double, tsdf_volume*>> heads;
+  for (auto& kv : s->queues)
+    if (!kv.second.empty() && kv.second.front().slot < 0)
+      heads.emplace_back(kv.second.front().arrival, kv.first);
+  std::sort(heads.begin(), heads.end());
+  for (const auto& h : heads) {
+    if (s->free_slots.empty()) return;
+    Pending& p = s->queues[h.second].front();
+    p.slot = s->free_slots.back();
+    s->free_slots.pop_back();
+    copy_in(s, p, p.slot, s->copy_stream);
+    cudaEventRecord(s->slot_copied[p.slot], s->copy_stream);
+  }
+}
+
 // Launch one batch (or one frame) from the queue heads. Returns false if
 // nothing was ready.
 bool launch_some(tsdf_server* s) {
@@ -80,11 +115,23 @@ bool launch_some(tsdf_server* s) {
   for (auto& kv : s->queues)
     if (!kv.second.empty() && s->busy[kv.first] == 0)
       ready.emplace_back(kv.second.front().arrival, kv.first);
-  if (ready.empty() || s->free_slots.empty() || s->events.empty()) return false;
+  if (ready.empty() || s->events.empty()) return false;
   std::sort(ready.begin(), ready.end());
+  if (s->mode == 0) {
+    // only heads whose copy is enqueued (every head has one while slots last)
+    ready.erase(std::remove_if(ready.begin(), ready.end(),
+                               [s](const std::pair<double, tsdf_volume*>& r) {
+                                 return s->queues[r.second].front().slot < 0;
+                               }),
+                ready.end());
+    if (ready.empty()) return false;
+  } else if (s->free_slots.empty()) {
+    return false;
+  }
   int take = s->mode == 1 ? 1 : s->max_batch;
   if (take > static_cast<int>(ready.size())) take = static_cast<int>(ready.size());
-  if (take > static_cast<int>(s->free_slots.size())) take = static_cast<int>(s->free_slots.size());
+  if (s->mode == 1 && take > static_cast<int>(s->free_slots.size()))
+    take = static_cast<int>(s->free_slots.size());
   InFlight f;
   std::vector<tsdf_frame> frames;
   frames.reserve(take);
@@ -92,8 +139,11 @@ bool launch_some(tsdf_server* s) {
     tsdf_volume* v = ready[i].second;
     Pending p = s->queues[v].front();
     s->queues[v].pop_front();
-    const int slot = s->free_slots.back();
-    s->free_slots.pop_back();
+    int slot = p.slot;
+    if (slot < 0) {  // mode 1: the copy goes on the launch stream, just before
+      slot = s->free_slots.back();
+      s->free_slots.pop_back();
+    }
     if (p.reset) {
       const tsdf_status rs = tsdf_volume_reset(v, s->stream);
       if (rs != TSDF_OK && s->sticky == TSDF_OK) s->sticky = rs;
@@ -101,8 +151,10 @@ bool launch_some(tsdf_server* s) {
     char* dst = s->staging + static_cast<size_t>(slot) * s->slot_bytes;
     const size_t npx = static_cast<size_t>(p.w) * p.h;
     const size_t dbytes = tsdf::align_up(npx * sizeof(float));
-    cudaMemcpyAsync(dst, p.depth, npx * sizeof(float), cudaMemcpyHostToDevice, s->stream);
-    if (p.rgb) cudaMemcpyAsync(dst + dbytes, p.rgb, npx * 3, cudaMemcpyHostToDevice, s->stream);
+    if (p.slot < 0)
+      copy_in(s, p, slot, s->stream);
+    else
+      cudaStreamWaitEvent(s->stream, s->slot_copied[slot], 0);
     tsdf_frame fr;
     fr.volume = v;
     fr.depth = reinterpret_cast<const float*>(dst);
@@ -187,6 +239,21 @@ tsdf_status tsdf_server_create(int mode, int max_batch, int max_inflight, int ma
     }
     s->events.push_back(ev);
   }
+  if (mode == 0) {
+    if (cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      s->copy_stream = nullptr;
+      tsdf_server_destroy(s);
+      return TSDF_ERR_CUDA;
+    }
+    s->slot_copied.assign(staging_frames, nullptr);
+    for (int i = 0; i < staging_frames; ++i) {
+      if (cudaEventCreateWithFlags(&s->slot_copied[i], cudaEventDisableTiming) != cudaSuccess) {
+        s->slot_copied[i] = nullptr;
+        tsdf_server_destroy(s);
+        return TSDF_ERR_CUDA;
+      }
+    }
+  }
   tsdf_status st = TSDF_OK;
   if (mode == 0) {
     st = tsdf_batch_create(max_batch, &s->batch);
@@ -205,6 +272,10 @@ void tsdf_server_destroy(tsdf_server* s) {
   cudaStreamSynchronize(s->stream);
   for (auto& f : s->inflight) s->events.push_back(f.ev);
   for (cudaEvent_t ev : s->events) cudaEventDestroy(ev);
+  if (s->copy_stream) cudaStreamSynchronize(s->copy_stream);
+  for (cudaEvent_t ev : s->slot_copied)
+    if (ev) cudaEventDestroy(ev);
+  if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
   if (s->batch) tsdf_batch_destroy(s->batch);
   if (s->staging) cudaFree(s->staging);
   delete s;
@@ -225,7 +296,9 @@ tsdf_status tsdf_server_submit(tsdf_server* s, const tsdf_request* r) {
 int tsdf_server_poll(tsdf_server* s, tsdf_completion* out, int capacity) {
   if (!s) return -1;
   retire(s);
+  if (s->mode == 0) copy_heads(s);
   while (static_cast<int>(s->inflight.size()) < s->max_inflight && launch_some(s)) {
+    if (s->mode == 0) copy_heads(s);
   }
   int n = 0;
   while (n < capacity && !s->done.empty()) {
