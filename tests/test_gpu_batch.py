@@ -163,3 +163,36 @@ def test_batch_rejects_bad_arguments():
     frames = tsdf.make_frames([(v.handle, d, c, f.intr, f.pose)] * 3)
     assert tsdf.tsdf_fuse_batch_async(batch.handle, frames, 3) == "INVALID_ARG"   # > max
     assert batch.set_option("allocate_mode", 0) == "INVALID_ARG"
+
+
+@pytest.mark.parametrize("use_graph", [0, 1])
+def test_batch_stages_one_at_a_time_equal_both(use_graph):
+    """TSDF_OPT_BATCH_STAGES: stage A of every frame in one call, then stage B
+    of the same frames in another, equals the oracle (as both stages in one
+    call do)."""
+    ss = sessions(6, seed=13)
+    vols = [new_volume(s["spec"]) for s in ss]
+    ba = tsdf.Batch(len(ss), fuse_mode=0, batch_stages=1, use_graph=use_graph)
+    bb = tsdf.Batch(len(ss), fuse_mode=0, batch_stages=2, use_graph=use_graph)
+    for k in range(2):
+        items = []
+        for s, v in zip(ss, vols):
+            f = frame_of(s, k)
+            d, c = dev(f)
+            items.append((v, d, c, f.intr, f.pose))
+        assert ba.fuse_async(items) == "OK"
+        assert bb.fuse_async(items) == "OK"
+        st, per = bb.status(len(ss))
+        assert st == "OK" and all(p == "OK" for p in per)
+    for s, v in zip(ss, vols):
+        ov = oracle.OracleVolume(s["spec"].voxel_size, s["spec"].truncation,
+                                 s["spec"].table_slots, s["spec"].pool_blocks)
+        for k in range(2):
+            assert ov.fuse_frame(frame_of(s, k)) == "OK"
+        gc, gx = sort_blocks(*v.export())
+        oc, ox = ov.export(double=True)
+        assert np.array_equal(gc, oc)
+        assert np.array_equal(gx[:, 1], ox[:, 1].astype(np.float32))
+        assert float(np.max(np.abs(gx[:, [0, 2, 3, 4]] - ox[:, [0, 2, 3, 4]]))) <= TOL
+    assert ba.set_option("batch_stages", 0) == "INVALID_ARG"
+    assert ba.set_option("batch_stages", 4) == "INVALID_ARG"
