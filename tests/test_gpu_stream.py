@@ -144,3 +144,24 @@ def test_stream_refuses_an_invalid_frame_before_enqueueing():
     assert v.block_count() == 0                            # nothing was fused
     assert tsdf.tsdf_fuse_frames_host(tsdf.make_host_frames(items[:1]))[0] == "OK"
     assert v.block_count() > 1000
+
+
+def test_l2_fetch_granularity_changes_no_result():
+    """tsdf_set_l2_fetch_bytes (a context-wide cache hint): the volume with a
+    32-byte fetch equals the oracle, the previous value comes back, and values
+    other than 0, 32, 64, 128 are refused."""
+    f = _frames([7])[0]
+    st, before = tsdf.tsdf_set_l2_fetch_bytes(32)
+    assert st == "OK"
+    try:
+        v, ov = _vol(), _oracle()
+        d, c = _pinned(f)
+        st, per = tsdf.tsdf_fuse_frames_host(tsdf.make_host_frames(
+            [(v.handle, d, c, f.intr, f.pose)]))
+        assert st == "OK"
+        assert ov.fuse_frame(f) == "OK"
+        assert _same_as_oracle(v, ov) > 500
+        assert tsdf.tsdf_set_l2_fetch_bytes(48)[0] == "INVALID_ARG"
+    finally:
+        st, cur = tsdf.tsdf_set_l2_fetch_bytes(before)
+    assert st == "OK" and cur == 32
