@@ -378,7 +378,9 @@ tsdf_status tsdf_batch_status(tsdf_batch* batch, void* stream, tsdf_status* per_
  * staging slots (frame i into slot i mod 2, after the kernel of frame i-2 has
  * finished reading it), then fused on `stream` exactly as
  * tsdf_fuse_frame_async fuses it, and its volume's error word is copied back
- * into pinned memory. The call waits once, for the whole sequence, then
+ * into pinned memory (right after the frame when a later frame of the call
+ * goes into the same volume, else after the last frame). The call waits
+ * once, for the whole sequence, then
  * writes status[i] for every frame: OK, the frame's error (which poisons its
  * volume), POISONED for a volume poisoned before the call or by an earlier
  * frame of it. Returns the first non-OK status, else OK.

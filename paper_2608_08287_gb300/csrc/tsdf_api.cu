@@ -301,6 +301,8 @@ void tsdf_volume_destroy(tsdf_volume* vol) {
   if (vol->stage) cudaFree(vol->stage);
   if (vol->stream_stage) cudaFree(vol->stream_stage);
   if (vol->err_words) cudaFreeHost(vol->err_words);
+  if (vol->err_gathered) cudaFreeHost(vol->err_gathered);
+  if (vol->err_dev) cudaFree(vol->err_dev);
   for (int b = 0; b < 2; ++b) {
     if (vol->ev_copied[b]) cudaEventDestroy(vol->ev_copied[b]);
     if (vol->ev_free[b]) cudaEventDestroy(vol->ev_free[b]);

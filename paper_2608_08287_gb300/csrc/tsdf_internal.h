@@ -57,7 +57,9 @@ struct tsdf_volume {
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t ev_copied[2] = {nullptr, nullptr};
   cudaEvent_t ev_free[2] = {nullptr, nullptr};
-  uint32_t* err_words = nullptr;
+  uint32_t* err_words = nullptr;      // pinned, one word per frame of a call
+  uint32_t* err_gathered = nullptr;   // pinned, the words gathered on the device
+  uint32_t* err_dev = nullptr;        // device, where they are gathered
   int err_capacity = 0;
 };
 

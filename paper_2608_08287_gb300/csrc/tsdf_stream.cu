@@ -12,12 +12,22 @@
 // has finished), and a pinned array of per-frame error words. All are made on
 // first use and grown when a call needs more; nothing is allocated while a
 // call's work is in flight.
+//
+// A frame's error word is read right after its kernel only when a later frame
+// of the call goes into the same volume (its sticky bits would otherwise mix
+// with the later frame's); the last frame of each volume is read after the
+// last kernel -- the words gathered by one small kernel into a device array,
+// copied back at once -- so a sequence of frames into distinct volumes runs
+// its kernels back to back.
 #include <cstring>
+#include <unordered_map>
+#include <vector>
 
 #include <cuda_runtime.h>
 
 #include "tsdf.h"
 #include "tsdf_internal.h"
+#include "tsdf_launch.h"
 
 using tsdf::align_up;
 using tsdf::as_stream;
@@ -25,6 +35,19 @@ using tsdf::decode_err;
 using tsdf::from_cuda;
 
 namespace {
+
+// Error words of up to kGather volumes copied into one device array.
+constexpr int kGather = 256;
+struct GatherArgs {
+  unsigned int* dst;
+  int n;
+  const unsigned int* src[kGather];
+};
+
+__global__ void gather_err_kernel(const __grid_constant__ GatherArgs a) {
+  const int i = static_cast<int>(threadIdx.x);
+  if (i < a.n) a.dst[i] = *reinterpret_cast<const volatile unsigned int*>(a.src[i]);
+}
 
 size_t frame_stage_bytes(const tsdf_frame& fr) {
   const size_t npx = static_cast<size_t>(fr.width) * static_cast<size_t>(fr.height);
@@ -69,11 +92,15 @@ tsdf_status ensure_resources(tsdf_volume* v, size_t slot_bytes, int n) {
   }
   if (v->err_capacity < n) {
     if (v->err_words) cudaFreeHost(v->err_words);
-    v->err_words = nullptr;
+    if (v->err_gathered) cudaFreeHost(v->err_gathered);
+    if (v->err_dev) cudaFree(v->err_dev);
+    v->err_words = v->err_gathered = v->err_dev = nullptr;
     v->err_capacity = 0;
     if (cudaMallocHost(reinterpret_cast<void**>(&v->err_words), sizeof(uint32_t) * n) !=
-        cudaSuccess) {
-      v->err_words = nullptr;
+            cudaSuccess ||
+        cudaMallocHost(reinterpret_cast<void**>(&v->err_gathered), sizeof(uint32_t) * n) !=
+            cudaSuccess ||
+        cudaMalloc(reinterpret_cast<void**>(&v->err_dev), sizeof(uint32_t) * n) != cudaSuccess) {
       cudaGetLastError();
       return TSDF_ERR_OUT_OF_MEMORY;
     }
@@ -105,6 +132,11 @@ extern "C" tsdf_status tsdf_fuse_frames_host(const tsdf_frame* frames, int n,
   }
   tsdf_status st = ensure_resources(owner, slot, n);
   if (st != TSDF_OK) return st;
+
+  // which frames have a later frame in the same volume
+  std::unordered_map<const tsdf_volume*, int> last_of;
+  last_of.reserve(static_cast<size_t>(n) * 2);
+  for (int i = 0; i < n; ++i) last_of[frames[i].volume] = i;
 
   cudaStream_t s = as_stream(stream);
   cudaStream_t cs = owner->copy_stream;
@@ -145,11 +177,31 @@ extern "C" tsdf_status tsdf_fuse_frames_host(const tsdf_frame* frames, int n,
       if (e == cudaSuccess) e = cudaErrorLaunchFailure;
       break;
     }
-    e = cudaMemcpyAsync(owner->err_words + i, &v->va.hdr->err, sizeof(uint32_t),
-                        cudaMemcpyDeviceToHost, s);
+    if (last_of[v] != i)
+      e = cudaMemcpyAsync(owner->err_words + i, &v->va.hdr->err, sizeof(uint32_t),
+                          cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaEventRecord(owner->ev_free[b], s);
     enqueued = i + 1;
   }
+  // the last frame of each volume: its word after every kernel of the call,
+  // gathered on the device and copied back in one piece
+  std::vector<int> gathered;
+  for (int i = 0; i < enqueued; ++i)
+    if (status[i] == TSDF_OK && last_of[frames[i].volume] == i) gathered.push_back(i);
+  for (size_t c = 0; c < gathered.size() && e == cudaSuccess; c += kGather) {
+    GatherArgs a;
+    a.dst = owner->err_dev + c;
+    a.n = static_cast<int>(gathered.size() - c < static_cast<size_t>(kGather)
+                               ? gathered.size() - c
+                               : kGather);
+    for (int j = 0; j < a.n; ++j) a.src[j] = &frames[gathered[c + j]].volume->va.hdr->err;
+    gather_err_kernel<<<1, kGather, 0, s>>>(a);
+    e = cudaGetLastError();
+    tsdf::note_launch();
+  }
+  if (e == cudaSuccess && !gathered.empty())
+    e = cudaMemcpyAsync(owner->err_gathered, owner->err_dev, sizeof(uint32_t) * gathered.size(),
+                        cudaMemcpyDeviceToHost, s);
   // one wait for the whole sequence (the copy stream's work is ordered
   // before `stream`'s through the events)
   const cudaError_t e_sync = cudaStreamSynchronize(s);
@@ -162,6 +214,8 @@ extern "C" tsdf_status tsdf_fuse_frames_host(const tsdf_frame* frames, int n,
       if (status[i] == TSDF_OK) status[i] = TSDF_ERR_CUDA;
     return TSDF_ERR_CUDA;
   }
+  for (size_t j = 0; j < gathered.size(); ++j)
+    owner->err_words[gathered[j]] = owner->err_gathered[j];
   // Per-frame status from the sticky error words: the first frame of a volume
   // whose word is set reports the error and poisons the volume; its later
   // frames did nothing on the device (the kernels skip a poisoned volume) and

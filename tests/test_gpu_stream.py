@@ -165,3 +165,26 @@ def test_l2_fetch_granularity_changes_no_result():
     finally:
         st, cur = tsdf.tsdf_set_l2_fetch_bytes(before)
     assert st == "OK" and cur == 32
+
+
+def test_stream_over_many_volumes_reads_every_status():
+    """More distinct volumes than one gather of status words holds (256): the
+    error words of the last frame of every volume are gathered in chunks. One
+    volume overflows; every other frame reports OK and equals the oracle."""
+    f = _frames([11], 160, 120)[0]
+    spec = synth.VolumeSpec(0.02, 0.08, 1 << 12, 1 << 11)
+    tiny = synth.VolumeSpec(0.02, 0.08, 1 << 12, 8)
+    n = 300
+    vols = [_vol(tiny if i == 271 else spec) for i in range(n)]
+    d, c = _pinned(f)
+    items = [(v.handle, d, c, f.intr, f.pose) for v in vols]
+    st, per = tsdf.tsdf_fuse_frames_host(tsdf.make_host_frames(items))
+    assert st == "POOL_FULL"
+    assert per[271] == "POOL_FULL"
+    assert all(p == "OK" for i, p in enumerate(per) if i != 271)
+    ov = _oracle(spec)
+    assert ov.fuse_frame(f) == "OK"
+    nb = ov.block_count()
+    assert all(v.block_count() == nb for i, v in enumerate(vols) if i != 271)
+    assert _same_as_oracle(vols[299], ov) == nb
+    assert vols[271].block_count() == tiny.pool_blocks
