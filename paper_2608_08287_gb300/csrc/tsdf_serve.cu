@@ -80,13 +80,22 @@ double now_s(const tsdf_server* s) {
   return std::chrono::duration<double>(std::chrono::steady_clock::now() - s->t0).count();
 }
 
+// A failed copy, event or stream call makes the server's status CUDA (the
+// first error is kept); the frames already accepted still complete.
+void note_cuda(tsdf_server* s, cudaError_t e) {
+  if (e == cudaSuccess) return;
+  cudaGetLastError();
+  if (s->sticky == TSDF_OK) s->sticky = TSDF_ERR_CUDA;
+}
+
 // Copy a frame into staging slot `slot` on stream cs.
 void copy_in(tsdf_server* s, const Pending& p, int slot, cudaStream_t cs) {
   char* dst = s->staging + static_cast<size_t>(slot) * s->slot_bytes;
   const size_t npx = static_cast<size_t>(p.w) * p.h;
   const size_t dbytes = tsdf::align_up(npx * sizeof(float));
-  cudaMemcpyAsync(dst, p.depth, npx * sizeof(float), cudaMemcpyHostToDevice, cs);
-  if (p.rgb) cudaMemcpyAsync(dst + dbytes, p.rgb, npx * 3, cudaMemcpyHostToDevice, cs);
+  note_cuda(s, cudaMemcpyAsync(dst, p.depth, npx * sizeof(float), cudaMemcpyHostToDevice, cs));
+  if (p.rgb)
+    note_cuda(s, cudaMemcpyAsync(dst + dbytes, p.rgb, npx * 3, cudaMemcpyHostToDevice, cs));
 }
 
 // Mode 0: give every session's head frame a staging slot and enqueue its copy
@@ -103,7 +112,7 @@ void copy_heads(tsdf_server* s) {
     p.slot = s->free_slots.back();
     s->free_slots.pop_back();
     copy_in(s, p, p.slot, s->copy_stream);
-    cudaEventRecord(s->slot_copied[p.slot], s->copy_stream);
+    note_cuda(s, cudaEventRecord(s->slot_copied[p.slot], s->copy_stream));
   }
 }
 
@@ -154,7 +163,7 @@ bool launch_some(tsdf_server* s) {
     if (p.slot < 0)
       copy_in(s, p, slot, s->stream);
     else
-      cudaStreamWaitEvent(s->stream, s->slot_copied[slot], 0);
+      note_cuda(s, cudaStreamWaitEvent(s->stream, s->slot_copied[slot], 0));
     tsdf_frame fr;
     fr.volume = v;
     fr.depth = reinterpret_cast<const float*>(dst);
@@ -180,7 +189,7 @@ bool launch_some(tsdf_server* s) {
   if (st != TSDF_OK && s->sticky == TSDF_OK) s->sticky = st;
   f.ev = s->events.back();
   s->events.pop_back();
-  cudaEventRecord(f.ev, s->stream);
+  note_cuda(s, cudaEventRecord(f.ev, s->stream));
   s->inflight.push_back(std::move(f));
   return true;
 }
@@ -188,7 +197,9 @@ bool launch_some(tsdf_server* s) {
 void retire(tsdf_server* s) {
   while (!s->inflight.empty()) {
     InFlight& f = s->inflight.front();
-    if (cudaEventQuery(f.ev) != cudaSuccess) break;
+    const cudaError_t q = cudaEventQuery(f.ev);
+    if (q == cudaErrorNotReady) break;
+    note_cuda(s, q);  // any other error: retired with the server's error status
     const double t = now_s(s);
     for (size_t i = 0; i < f.frames.size(); ++i) {
       const Pending& p = f.frames[i];
