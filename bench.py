@@ -963,6 +963,83 @@ def run_load_sweep(args, torch, tsdf, rendered):
 PROBE_CASE_LOADS = (0.1, 0.9)
 
 
+BATCH_CASE_SESSIONS = 16
+BATCH_CASE_POOL = 1 << 13
+
+
+def run_batch_profile_case(args):
+    """The batched fused kernel on a case small enough for an ncu capture of
+    all its sections: 16 sessions, alternately 320x240 and 160x120 room frames
+    of the session classes (the 640x480 class is left out), each into its own
+    empty volume with its class's table and a pool of 2^13 blocks (more than a
+    frame of these classes touches), so the device holds about 1.5 GB. The
+    3,040 tiles are at least the 2,048 a batch needs to replay its CUDA graph
+    of the persistent launch, the configuration the 64-session workload runs.
+    Each rep resets the volumes and scrubs L2 outside the CUDA events around
+    the batch; with --batch-case-reps 0 there is one warm-up batch and one
+    more, with no scrub (for ncu -s 1 -c 1, which flushes caches itself)."""
+    import torch
+    from paper_2608_08287_gb300 import serving, synth, tsdf
+    from paper_2608_08287_gb300.build import build_library
+    build_library()
+    torch.cuda.set_device(0)
+    classes = [(320, 240), (160, 120)]
+    sess = []
+    for i in range(BATCH_CASE_SESSIONS):
+        w, h = classes[i % 2]
+        cs = serving.SESSION_CLASSES[(w, h)]
+        spec = synth.VolumeSpec(cs.voxel_size, cs.truncation, cs.table_slots, BATCH_CASE_POOL)
+        sess.append((spec, synth.room_frame(12 * (i % 24), width=w, height=h)))
+    work = oracle_work_counts([(f.depth, f.rgb, np.asarray(f.intr, np.float32),
+                                np.asarray(f.pose, np.float32), sp) for sp, f in sess], None)
+    sums = [sum(x) for x in zip(*[stage_bytes(wk) for wk in work])]
+    points = sum(wk["points"] for wk in work)
+    stream = torch.cuda.Stream()
+    sp_ = stream.cuda_stream
+    vols = [tsdf.Volume(sp.voxel_size, sp.truncation, sp.table_slots, sp.pool_blocks)
+            for sp, _ in sess]
+    dev = [(torch.from_numpy(f.depth).cuda(), torch.from_numpy(f.rgb).cuda()) for _, f in sess]
+    items = [(v, d, c, f.intr, f.pose) for v, (d, c), (_, f) in zip(vols, dev, sess)]
+    batch = tsdf.Batch(len(sess), use_graph=1)
+    reps = args.batch_case_reps
+    flush = scrub = None
+    if reps > 0:
+        flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+        scrub = torch.ones(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    times = []
+    for i in range(1 + max(reps, 1)):
+        for v in vols:
+            assert v.reset(sp_) == "OK"
+        if flush is not None:
+            with torch.cuda.stream(stream):
+                l2_scrub(flush, scrub, i)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        assert batch.fuse_async(items, stream=sp_) == "OK"
+        b.record(stream)
+        stream.synchronize()
+        if i >= 1:
+            times.append(a.elapsed_time(b))
+    st, _ = batch.status(len(sess), stream=sp_)
+    assert st == "OK", st
+    counts_match = all(v.block_count(sp_) == wk["blocks"] for v, wk in zip(vols, work))
+    batch.close()
+    for v in vols:
+        v.close()
+    ms = float(np.median(times))
+    hbm, peak_kind = peaks()
+    return {"case": "batch_tile_fused_kernel, 16 sessions (8 x 320x240, 8 x 160x120 room "
+                    "frames), each into an empty volume",
+            "tiles": sum(((w + 15) // 16) * ((h + 15) // 16) for w, h in
+                         (classes[i % 2] for i in range(BATCH_CASE_SESSIONS))),
+            "points": int(points), "reps": reps, "ms_median": round(ms, 4),
+            "pts_per_s": round(points / (ms / 1e3), 1),
+            "algorithmic_bytes": int(sums[2]), "peak_gbs": hbm, "peak_kind": peak_kind,
+            "frac": round(sums[2] / (ms * 1e6) / hbm, 4),
+            "gpu_block_counts_match_oracle": bool(counts_match)}
+
+
 def run_probe_policy_case(args):
     """The probe-load policy case (Section 6.2: whether a probe read is kept in
     L1 decided speed there). The room orbit (640x480) is fused into a table
@@ -1258,6 +1335,12 @@ def main():
     ap.add_argument("--probe-case-reps", type=int, default=5,
                     help="timed repetitions per launch of the probe-load policy case "
                          "(0: one launch each and no L2 scrub, for an ncu capture)")
+    ap.add_argument("--batch-profile-case", action="store_true",
+                    help="only the batched fused kernel on a 16-session case of about 1.5 GB "
+                         "(a small command for an ncu capture of the batched kernel)")
+    ap.add_argument("--batch-case-reps", type=int, default=20,
+                    help="timed batches of the batch profile case (0: one batch after a "
+                         "warm-up, no L2 scrub, for an ncu capture)")
     ap.add_argument("--small-steps", type=int, default=100,
                     help="timed steps per threads-per-point setting on the small frames")
     args = ap.parse_args()
@@ -1276,6 +1359,11 @@ def main():
     if args.probe_policy_case:
         if rank == 0:
             print(json.dumps(run_probe_policy_case(args)), flush=True)
+        return
+
+    if args.batch_profile_case:
+        if rank == 0:
+            print(json.dumps(run_batch_profile_case(args)), flush=True)
         return
 
     if args.extraction_only:
