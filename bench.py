@@ -623,9 +623,11 @@ def run_e2e(args, vol, frames, torch, tsdf, sp, stream, flush, scrub, world=1):
 
 def run_batched(args, torch, tsdf, serving, bank):
     """Config-4 style: 64 sessions (mixed 160x120 / 320x240 / 640x480, tables
-    2^16..2^20), one frame each per step into fresh volumes, as one batch
-    (persistent launches replayed from a CUDA graph) against a loop of
-    per-frame launches. Device time per step, L2 scrubbed between steps."""
+    2^16..2^20), one frame each per step into fresh volumes, as one batch call
+    -- its default form, one launch per frame over the batch's 8 streams, and
+    its persistent form, one launch for all frames replayed from a CUDA graph
+    -- against a loop of per-frame launches on one stream. Device time per
+    step, L2 scrubbed between steps."""
     n = BATCH_SESSIONS
     res = batch_resolutions(n)
     vols = []
@@ -639,7 +641,8 @@ def run_batched(args, torch, tsdf, serving, bank):
         depth_h, rgb_h, intr, pose, pts = bank.get(r, i)
         dev.append((depth_h.cuda(), rgb_h.cuda(), intr, pose, pts))
     points = sum(x[4] for x in dev)
-    batch = tsdf.Batch(n, use_graph=1)
+    batch = tsdf.Batch(n, use_graph=1)                          # per-frame launches, 8 streams
+    batch_p = tsdf.Batch(n, use_graph=1, batch_streams=0)       # one persistent launch (graph)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     scrub = torch.ones(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     items = [(v, d, c, intr, pose) for v, (d, c, intr, pose, _) in zip(vols, dev)]
@@ -666,6 +669,9 @@ def run_batched(args, torch, tsdf, serving, bank):
     def batched():
         assert batch.fuse_async(items, stream=sp_) == "OK"
 
+    def persistent():
+        assert batch_p.fuse_async(items, stream=sp_) == "OK"
+
     def per_frame():
         for v, d, c, intr, pose in items:
             assert tsdf.tsdf_fuse_frame_async(v.handle, d, d.shape[1], d.shape[0], intr, pose,
@@ -675,6 +681,11 @@ def run_batched(args, torch, tsdf, serving, bank):
     tb = timed(batched, args.batch_steps)
     st, _ = batch.status(n, stream=sp_)
     assert st == "OK", st
+    timed(persistent, 3)
+    tpers = timed(persistent, args.batch_steps)
+    st, _ = batch_p.status(n, stream=sp_)
+    assert st == "OK", st
+    batch_p.close()
     timed(per_frame, 3)
     tp = timed(per_frame, args.batch_steps)
     for v in vols:
@@ -684,9 +695,9 @@ def run_batched(args, torch, tsdf, serving, bank):
     # allocator) as one persistent launch over the 64 frames, then stage B
     # (per-thread scatter) as another, each replayed from its own graph
     batch_a = tsdf.Batch(n, use_graph=1, fuse_mode=0, allocate_mode=1, integrate_mode=0,
-                         batch_stages=1)
+                         batch_stages=1, batch_streams=0)
     batch_b = tsdf.Batch(n, use_graph=1, fuse_mode=0, allocate_mode=1, integrate_mode=0,
-                         batch_stages=2)
+                         batch_stages=2, batch_streams=0)
     ta_, tb_ = [], []
     for i in range(3 + args.batch_steps):
         prep(i)
@@ -724,9 +735,13 @@ def run_batched(args, torch, tsdf, serving, bank):
                     "algorithmic_bytes": int(sums[1]),
                     "frac": round(sums[1] / (sb_ms * 1e6) / hbm, 4)},
         "two_stage_pts_per_s": round(points / ((sa_ms + sb_ms) / 1e3), 1),
-        "fused": {"kernel": "batch_tile_fused_kernel", "ms": round(float(np.mean(tb)), 4),
-                  "algorithmic_bytes": int(sums[2]),
-                  "frac": round(sums[2] / (float(np.mean(tb)) * 1e6) / hbm, 4)}}
+        "fused": {"kernel": "tile_fused_kernel, one launch per frame over 8 streams (default)",
+                  "ms": round(float(np.mean(tb)), 4), "algorithmic_bytes": int(sums[2]),
+                  "frac": round(sums[2] / (float(np.mean(tb)) * 1e6) / hbm, 4)},
+        "fused_persistent": {"kernel": "batch_tile_fused_kernel (one persistent launch)",
+                             "ms": round(float(np.mean(tpers)), 4),
+                             "algorithmic_bytes": int(sums[2]),
+                             "frac": round(sums[2] / (float(np.mean(tpers)) * 1e6) / hbm, 4)}}
     # the batch autotuner on the same frames (volumes empty before and after)
     for v in vols:
         assert v.reset(sp_) == "OK"
@@ -739,15 +754,19 @@ def run_batched(args, torch, tsdf, serving, bank):
         v.close()
     batch.close()
     mb, mp_, mt = float(np.mean(tb)), float(np.mean(tp)), float(np.mean(tt))
+    mpers = float(np.mean(tpers))
     return {"sessions": n, "points_per_step": int(points),
             "batched_pts_per_s": round(points / (mb / 1e3), 1), "batched_ms_per_step": round(mb, 4),
+            "batched_form": "default: one launch per frame, largest first, over 8 streams",
+            "persistent_pts_per_s": round(points / (mpers / 1e3), 1),
+            "persistent_ms_per_step": round(mpers, 4),
             "per_frame_pts_per_s": round(points / (mp_ / 1e3), 1),
             "per_frame_ms_per_step": round(mp_, 4),
             "autotuned_pts_per_s": round(points / (mt / 1e3), 1),
             "autotuned_ms_per_step": round(mt, 4), "autotuned_config": tuning,
-            "launches_per_step": {"batched": 1, "per_frame": n},
+            "launches_per_step": {"batched": n, "persistent": 1, "per_frame": n},
             "stage_rooflines": stage_rooflines,
-            "steps": args.batch_steps, "graph": True}
+            "steps": args.batch_steps, "graph": "persistent form only"}
 
 
 def run_serving(args, torch, serving, bank):
@@ -1000,7 +1019,7 @@ def run_batch_profile_case(args):
             for sp, _ in sess]
     dev = [(torch.from_numpy(f.depth).cuda(), torch.from_numpy(f.rgb).cuda()) for _, f in sess]
     items = [(v, d, c, f.intr, f.pose) for v, (d, c), (_, f) in zip(vols, dev, sess)]
-    batch = tsdf.Batch(len(sess), use_graph=1)
+    batch = tsdf.Batch(len(sess), use_graph=1, batch_streams=0)   # the persistent form
     reps = args.batch_case_reps
     flush = scrub = None
     if reps > 0:

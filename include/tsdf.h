@@ -198,7 +198,17 @@ typedef enum tsdf_option {
    * stage B alone, for frames whose stage A ran before (a separate call on
    * the same frames) -- so that each stage can be timed on its own. Other
    * fuse modes ignore it. */
-  TSDF_OPT_BATCH_STAGES = 11
+  TSDF_OPT_BATCH_STAGES = 11,
+  /* Batches only: 0 = every frame of a call in one persistent launch per
+   * stage (the batched kernels; TSDF_OPT_CTAS_PER_SM and TSDF_OPT_USE_GRAPH
+   * apply); k = 1..16 = every frame in a launch of its own -- the
+   * single-frame kernels, with the batch's strategy options and the threads
+   * per point chosen per frame as for a volume set to 0 -- the frames taken
+   * largest first and dealt round-robin over k streams the batch owns, which
+   * wait for `stream` before their first launch and which `stream` waits for
+   * after their last (concurrent kernels fill the GPU where one small frame
+   * cannot). Default 8. The result is the same for every value. */
+  TSDF_OPT_BATCH_STREAMS = 12
 } tsdf_option;
 
 /* ---------------------------------------------------------------------------
@@ -345,11 +355,15 @@ void tsdf_batch_destroy(tsdf_batch* batch);
 
 /* TSDF_OPT_PROBE_LOAD, TSDF_OPT_ALLOCATE_MODE (1 or 2), TSDF_OPT_INTEGRATE_MODE,
  * TSDF_OPT_FUSE_MODE (default 2, as for volumes), TSDF_OPT_CTAS_PER_SM,
- * TSDF_OPT_USE_GRAPH. */
+ * TSDF_OPT_USE_GRAPH, TSDF_OPT_BATCH_STAGES, TSDF_OPT_BATCH_STREAMS (setting
+ * it above the streams the batch has creates the missing streams and their
+ * events: TSDF_ERR_CUDA if that fails). */
 tsdf_status tsdf_batch_set_option(tsdf_batch* batch, tsdf_option opt, int64_t value);
 
 /* Enqueue the fusion of n frames (1 <= n <= max_frames), each into a distinct
- * volume, on `stream`: allocation of every frame, then integration of every
+ * volume, on `stream`: with TSDF_OPT_BATCH_STREAMS k > 0 (the default) one
+ * launch per frame over the batch's k streams, forked from and joined back
+ * into `stream`; with 0, allocation of every frame, then integration of every
  * frame (two persistent launches), or one fused launch. Returns after
  * enqueueing; it may first wait for the batch's launch before last (the
  * session tables are double-buffered). Frame buffers must stay valid until
@@ -408,6 +422,7 @@ typedef struct tsdf_tuning {
   float default_ms;           /* median time of the default configuration */
   int threads_per_point;      /* volumes: the chosen TSDF_OPT_THREADS_PER_POINT, 0 = automatic
                                  (1 for a batch) */
+  int batch_streams;          /* batches: the chosen TSDF_OPT_BATCH_STREAMS (0 for a volume) */
 } tsdf_tuning;
 
 /* Tune `vol` for this frame: every stage A x stage B strategy, the fused
@@ -426,7 +441,9 @@ tsdf_status tsdf_autotune_frame(tsdf_volume* vol, const float* depth_dev, int wi
                                 tsdf_tuning* out);
 
 /* Tune `batch` for these frames: the strategies, then the CTAs-per-SM cap of
- * the persistent grid (1..4 or all), then graph replay on or off. Every
+ * the persistent grid (1..4 or all), then graph replay on or off (all with
+ * TSDF_OPT_BATCH_STREAMS 0), then one launch per frame over 4, 8 and 16
+ * streams with the best strategy. Every
  * frame's volume must be empty (nothing fused since creation or reset;
  * TSDF_ERR_INVALID_ARG otherwise): the volumes are reset before each
  * repetition and are left empty. The batch's options are set to the fastest

@@ -182,29 +182,31 @@ tsdf_status make_frame(const tsdf_volume* v, const float* depth, int w, int h,
   return TSDF_OK;
 }
 
+int auto_threads_per_point(int fuse_mode, int probe_load, int half_band, int sm_count, int width,
+                           int height) {
+  if (fuse_mode != 2 || probe_load != kLoadCached ||
+      (half_band != 2 && half_band != 4 && half_band != 8))
+    return 1;
+  const long long tiles = static_cast<long long>((width + 15) / 16) * ((height + 15) / 16);
+  const long long slots = 4ll * (sm_count > 0 ? sm_count : 1);
+  int t = 1;
+  while (t < 4 && tiles * (2 * t) <= slots) t *= 2;
+  return t;
+}
+
 }  // namespace tsdf
 
 using tsdf::make_frame;
 
 namespace {
 
-// Threads per point of the fused tile kernel for a width x height frame. An
-// explicit setting is taken as it is. Automatic (0): the largest of 1, 2, 4
-// whose CTAs (one per 16 x 16/TPP pixel tile) still fit the GPU's resident
-// slots at four CTAs per SM -- a frame that fills the GPU keeps one thread
-// per point -- where the split walk exists (fuse mode 2, the default probe
-// load, half band 2, 4 or 8), else 1.
+// Threads per point of the fused tile kernel for a width x height frame: an
+// explicit setting as it is, else the automatic choice.
 int threads_per_point(const tsdf_volume* vol, int width, int height) {
   if (vol->fuse_mode != 2) return 1;
   if (vol->threads_per_point != 0) return vol->threads_per_point;
-  if (vol->probe_load != tsdf::kLoadCached ||
-      (vol->half_band != 2 && vol->half_band != 4 && vol->half_band != 8))
-    return 1;
-  const long long tiles = static_cast<long long>((width + 15) / 16) * ((height + 15) / 16);
-  const long long slots = 4ll * (vol->sm_count > 0 ? vol->sm_count : 1);
-  int t = 1;
-  while (t < 4 && tiles * (2 * t) <= slots) t *= 2;
-  return t;
+  return tsdf::auto_threads_per_point(vol->fuse_mode, vol->probe_load, vol->half_band,
+                                      vol->sm_count, width, height);
 }
 
 // Host-side header of a checkpoint, followed by the volume's whole device

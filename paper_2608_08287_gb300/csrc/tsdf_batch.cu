@@ -1,5 +1,14 @@
-// Batched fusion: many frames, each into its own volume, in one launch per
-// stage (or one fused launch), optionally replayed from a CUDA graph.
+// Batched fusion: many frames, each into its own volume, either as one launch
+// per frame over several streams the batch owns (TSDF_OPT_BATCH_STREAMS > 0,
+// the default), or in one persistent launch per stage (or one fused launch),
+// optionally replayed from a CUDA graph.
+//
+// Per-frame launches: the frames are taken largest first and dealt
+// round-robin over the batch's streams, so the big frames start together and
+// the small ones fill the GPU around them; each stream waits for an event on
+// the caller's stream before its first launch, and the caller's stream waits
+// for each stream's last. Each frame runs the single-frame kernels with its
+// arguments in the kernel's parameter space.
 //
 // A batch owns two session tables (double buffering): a pinned host copy the
 // caller's frames are written into, and a device copy the kernels read. Each
@@ -9,6 +18,7 @@
 // captured once per configuration and replayed; the kernels' grids are
 // persistent, so one graph serves batches of any composition. Batches too small
 // to fill that grid are launched directly with a grid of their own size.
+#include <algorithm>
 #include <cstring>
 #include <new>
 
@@ -43,6 +53,15 @@ struct tsdf_batch {
   cudaStream_t capture = nullptr;
   cudaGraphExec_t exec[2] = {nullptr, nullptr};
   long long exec_key[2] = {-1, -1};
+  // per-frame launches (TSDF_OPT_BATCH_STREAMS): lanes in use, lanes made,
+  // the lanes and the event each records after its last launch, the fork
+  // event, and the launch order
+  int lanes = 0;
+  int lanes_made = 0;
+  cudaStream_t lane[16] = {};
+  cudaEvent_t lane_done[16] = {};
+  cudaEvent_t fork = nullptr;
+  int* order = nullptr;
 };
 
 namespace {
@@ -75,6 +94,81 @@ cudaError_t enqueue(tsdf_batch* b, int slot, size_t bytes, int grid_limit, bool 
 // own size: a replayed graph's persistent grid would mostly idle.
 constexpr int kGraphMinTiles = 2048;
 
+constexpr int kMaxLanes = 16;
+constexpr int kDefaultLanes = 8;
+
+// Make lanes up to k (streams that do not synchronise with the legacy default
+// stream, and their events).
+cudaError_t make_lanes(tsdf_batch* b, int k) {
+  if (!b->fork) {
+    const cudaError_t e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      b->fork = nullptr;
+      return e;
+    }
+  }
+  while (b->lanes_made < k) {
+    const int i = b->lanes_made;
+    cudaError_t e = cudaStreamCreateWithFlags(&b->lane[i], cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      b->lane[i] = nullptr;
+      return e;
+    }
+    e = cudaEventCreateWithFlags(&b->lane_done[i], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      cudaStreamDestroy(b->lane[i]);
+      b->lane[i] = nullptr;
+      b->lane_done[i] = nullptr;
+      return e;
+    }
+    ++b->lanes_made;
+  }
+  return cudaSuccess;
+}
+
+// Launch one frame's fusion with the batch's strategy on stream s.
+cudaError_t launch_one(const tsdf_batch* b, const tsdf::SessionArgs& a, int width, int height,
+                       int half_band, int sm_count, cudaStream_t s) {
+  if (b->fuse_mode != 0) {
+    const int tpp = tsdf::auto_threads_per_point(b->fuse_mode, b->probe_load, half_band,
+                                                 sm_count, width, height);
+    return tsdf::launch_fused(a.f, a.vol, b->probe_load, b->fuse_mode, tpp, s);
+  }
+  cudaError_t e = cudaSuccess;
+  if (b->stages & 1) e = tsdf::launch_allocate(a.f, a.vol, b->probe_load, b->allocate_mode, s);
+  if (e == cudaSuccess && (b->stages & 2)) e = tsdf::launch_integrate(a.f, a.vol, b->integrate_mode, s);
+  return e;
+}
+
+// Per-frame launches of the n frames whose arguments are in S, over the
+// batch's lanes, forked from and joined back into s.
+cudaError_t enqueue_lanes(tsdf_batch* b, const tsdf_frame* frames,
+                          const tsdf::SessionArgs* S, int n, cudaStream_t s) {
+  for (int i = 0; i < n; ++i) b->order[i] = i;
+  std::stable_sort(b->order, b->order + n, [frames](int x, int y) {
+    return static_cast<long long>(frames[x].width) * frames[x].height >
+           static_cast<long long>(frames[y].width) * frames[y].height;
+  });
+  const int lanes = std::min(b->lanes, n);
+  cudaError_t e = cudaEventRecord(b->fork, s);
+  for (int j = 0; j < lanes && e == cudaSuccess; ++j) e = cudaStreamWaitEvent(b->lane[j], b->fork, 0);
+  if (e != cudaSuccess) return e;
+  for (int k = 0; k < n && e == cudaSuccess; ++k) {
+    const int i = b->order[k];
+    const tsdf_volume* v = frames[i].volume;
+    e = launch_one(b, S[i], frames[i].width, frames[i].height, v->half_band, v->sm_count,
+                   b->lane[k % lanes]);
+  }
+  // the join is enqueued even after a failed launch, so `s` stays ordered
+  // after whatever the lanes did take
+  for (int j = 0; j < lanes; ++j) {
+    cudaError_t ej = cudaEventRecord(b->lane_done[j], b->lane[j]);
+    if (ej == cudaSuccess) ej = cudaStreamWaitEvent(s, b->lane_done[j], 0);
+    if (e == cudaSuccess) e = ej;
+  }
+  return e;
+}
+
 }  // namespace
 
 extern "C" {
@@ -97,8 +191,11 @@ tsdf_status tsdf_batch_create(int max_frames, tsdf_batch** out) {
   if (e == cudaSuccess) e = cudaMalloc(&b->status_dev, sizeof(unsigned) * max_frames);
   if (e == cudaSuccess) e = cudaMallocHost(&b->status_host, sizeof(unsigned) * max_frames);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = make_lanes(b, kDefaultLanes);
+  if (e == cudaSuccess) b->lanes = kDefaultLanes;
   b->last_vols = new (std::nothrow) tsdf_volume*[max_frames];
-  if (e != cudaSuccess || !b->last_vols) {
+  b->order = new (std::nothrow) int[max_frames];
+  if (e != cudaSuccess || !b->last_vols || !b->order) {
     cudaGetLastError();
     tsdf_batch_destroy(b);
     return e == cudaErrorMemoryAllocation || e == cudaSuccess ? TSDF_ERR_OUT_OF_MEMORY
@@ -120,7 +217,13 @@ void tsdf_batch_destroy(tsdf_batch* b) {
   if (b->status_dev) cudaFree(b->status_dev);
   if (b->status_host) cudaFreeHost(b->status_host);
   if (b->capture) cudaStreamDestroy(b->capture);
+  for (int i = 0; i < b->lanes_made; ++i) {
+    cudaStreamDestroy(b->lane[i]);
+    cudaEventDestroy(b->lane_done[i]);
+  }
+  if (b->fork) cudaEventDestroy(b->fork);
   delete[] b->last_vols;
+  delete[] b->order;
   delete b;
 }
 
@@ -155,6 +258,16 @@ tsdf_status tsdf_batch_set_option(tsdf_batch* b, tsdf_option opt, int64_t value)
       if (value < 1 || value > 3) return TSDF_ERR_INVALID_ARG;
       b->stages = static_cast<int>(value);
       return TSDF_OK;
+    case TSDF_OPT_BATCH_STREAMS: {
+      if (value < 0 || value > kMaxLanes) return TSDF_ERR_INVALID_ARG;
+      const cudaError_t e = make_lanes(b, static_cast<int>(value));
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return TSDF_ERR_CUDA;
+      }
+      b->lanes = static_cast<int>(value);
+      return TSDF_OK;
+    }
     default:
       return TSDF_ERR_INVALID_ARG;
   }
@@ -206,6 +319,19 @@ tsdf_status tsdf_fuse_batch_async(tsdf_batch* b, const tsdf_frame* frames, int n
   b->last_n = n;
   cudaStream_t s = as_stream(stream);
   cudaError_t e = cudaSuccess;
+  if (b->lanes > 0) {
+    e = enqueue_lanes(b, frames, S, n, s);
+    // the session table still goes to the device: tsdf_batch_status reads
+    // each frame's volume header through it
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(b->table_dev[slot], b->table_host[slot],
+                          sizeof(tsdf::BatchHeader) + static_cast<size_t>(n) *
+                                                          sizeof(tsdf::SessionArgs),
+                          cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaEventRecord(b->done[slot], s);
+    b->used[slot] = true;
+    return from_cuda(e);
+  }
   if (b->use_graph && tiles >= kGraphMinTiles) {
     const long long key = config_key(b, all_m4);
     if (b->exec_key[slot] != key) {

@@ -25,6 +25,14 @@ inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s
 tsdf_status from_cuda(cudaError_t e);
 tsdf_status decode_err(uint32_t err);
 
+// Threads per point of the fused tile kernel chosen for a width x height
+// frame: the largest of 1, 2, 4 whose CTAs (one per 16 x 16/TPP pixel tile)
+// still fit the GPU's resident slots at four CTAs per SM -- a frame that fills
+// the GPU keeps one thread per point -- where the split walk exists (fuse
+// mode 2, the default probe load, half band 2, 4 or 8), else 1.
+int auto_threads_per_point(int fuse_mode, int probe_load, int half_band, int sm_count, int width,
+                           int height);
+
 }  // namespace tsdf
 
 struct tsdf_volume {

@@ -10,9 +10,11 @@
 //
 // A batch is tuned on its frames' volumes, which must be empty: before every
 // repetition they are reset (so every repetition fuses into empty volumes),
-// and they are left empty. The search is staged: the strategies with the
-// persistent grid at full occupancy and graphs on, then the CTAs-per-SM cap
-// of the best strategy, then graphs off.
+// and they are left empty. The search is staged: the default (one launch per
+// frame over 8 streams), the strategies with the persistent grid at full
+// occupancy and graphs on, then the CTAs-per-SM cap of the best of those,
+// then graphs off, then the best persistent strategy launched per frame over
+// 4, 8 and 16 streams.
 //
 // Each configuration's time is the median of `reps` repetitions after one
 // untimed warm-up, with CUDA events on the caller's stream.
@@ -29,6 +31,7 @@ namespace {
 struct Config {
   int allocate_mode, integrate_mode, fuse_mode, probe_load, ctas_per_sm, use_graph;
   int threads_per_point = 1;
+  int batch_streams = 0;  // batches: TSDF_OPT_BATCH_STREAMS
 };
 
 float median(std::vector<float> v) {
@@ -86,6 +89,7 @@ tsdf_status apply_batch(tsdf_batch* b, const Config& c) {
   if (st == TSDF_OK) st = tsdf_batch_set_option(b, TSDF_OPT_PROBE_LOAD, c.probe_load);
   if (st == TSDF_OK) st = tsdf_batch_set_option(b, TSDF_OPT_CTAS_PER_SM, c.ctas_per_sm);
   if (st == TSDF_OK) st = tsdf_batch_set_option(b, TSDF_OPT_USE_GRAPH, c.use_graph);
+  if (st == TSDF_OK) st = tsdf_batch_set_option(b, TSDF_OPT_BATCH_STREAMS, c.batch_streams);
   return st;
 }
 
@@ -100,6 +104,7 @@ void fill(tsdf_tuning* out, const Config& c, float best, float dflt, int n) {
   out->best_ms = best;
   out->default_ms = dflt;
   out->threads_per_point = c.threads_per_point;
+  out->batch_streams = c.batch_streams;
 }
 
 }  // namespace
@@ -219,39 +224,64 @@ tsdf_status tsdf_batch_autotune(tsdf_batch* batch, const tsdf_frame* frames, int
   };
 
   int tried = 0;
-  const Config dflt{1, 0, 2, 0, 0, 1, 1};
+  // the batch's defaults: the fused tile kernel, one launch per frame over 8
+  // streams
+  const Config dflt{1, 0, 2, 0, 0, 1, 1, 8};
   Config best = dflt;
   float best_ms = 0.0f, dflt_ms = 0.0f;
   if (st == TSDF_OK) st = run(dflt, &dflt_ms);
   ++tried;
   best_ms = dflt_ms;
+  // the best persistent-launch configuration (TSDF_OPT_BATCH_STREAMS 0)
+  Config best_p{1, 0, 2, 0, 0, 1, 1, 0};
+  float best_p_ms = -1.0f;
   auto consider = [&](const Config& c) {
     if (st != TSDF_OK) return;
     float ms = 0.0f;
     st = run(c, &ms);
     ++tried;
-    if (st == TSDF_OK && ms < best_ms) {
+    if (st != TSDF_OK) return;
+    if (ms < best_ms) {
       best_ms = ms;
       best = c;
     }
+    if (c.batch_streams == 0 && (best_p_ms < 0.0f || ms < best_p_ms)) {
+      best_p_ms = ms;
+      best_p = c;
+    }
   };
-  // stage 1: strategies (the batched kernels take stage A strategies 1 and 2)
-  consider({1, 0, 0, 0, 0, 1, 1});
-  consider({1, 1, 0, 0, 0, 1, 1});
-  consider({2, 0, 0, 0, 0, 1, 1});
-  consider({2, 1, 0, 0, 0, 1, 1});
-  consider({1, 0, 1, 0, 0, 1, 1});
+  // stage 1: strategies in one persistent launch (the batched kernels take
+  // stage A strategies 1 and 2)
+  consider({1, 0, 2, 0, 0, 1, 1, 0});
+  consider({1, 0, 0, 0, 0, 1, 1, 0});
+  consider({1, 1, 0, 0, 0, 1, 1, 0});
+  consider({2, 0, 0, 0, 0, 1, 1, 0});
+  consider({2, 1, 0, 0, 0, 1, 1, 0});
+  consider({1, 0, 1, 0, 0, 1, 1, 0});
   // stage 2: resident CTAs per SM of the persistent grid
-  const Config strat = best;
+  const Config strat = best_p;
   for (int f = 1; f <= 4; ++f) {
     Config c = strat;
     c.ctas_per_sm = f;
     consider(c);
   }
   // stage 3: direct launches instead of graph replays
-  Config direct = best;
+  Config direct = best_p;
   direct.use_graph = 0;
   consider(direct);
+  // stage 4: the best persistent strategy launched per frame over 4, 8 and 16
+  // streams (8 with the default strategy was timed first)
+  for (int k = 4; k <= 16; k *= 2) {
+    Config c = best_p;
+    c.ctas_per_sm = 0;
+    c.use_graph = 1;
+    c.batch_streams = k;
+    if (k == 8 && c.allocate_mode == dflt.allocate_mode &&
+        c.integrate_mode == dflt.integrate_mode && c.fuse_mode == dflt.fuse_mode &&
+        c.probe_load == dflt.probe_load)
+      continue;
+    consider(c);
+  }
   for (int i = 0; i < n && st == TSDF_OK; ++i) st = tsdf_volume_reset(frames[i].volume, stream);
   evict.release(s);
   if (st == TSDF_OK) st = tsdf::from_cuda(cudaStreamSynchronize(s));

@@ -25,7 +25,7 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OUT_OF_MEMORY", 3: "POOL_FULL", 4: "TAB
 OPTIONS = {"probe_load": 0, "publish_timeout_ns": 1, "integrate_mode": 2, "threads": 3,
            "allocate_mode": 4, "fuse_mode": 5, "ctas_per_sm": 6, "use_graph": 7,
            "slot_index": 8, "probe_bound": 9, "threads_per_point": 10,
-           "batch_stages": 11}
+           "batch_stages": 11, "batch_streams": 12}
 ERRBITS = {"POOL_FULL": 1, "TABLE_FULL": 2, "PUBLISH_TIMEOUT": 4, "BOUNDS": 8}
 EMPTY_KEY = 0xFFFFFFFFFFFFFFFF
 NOALLOC_MAX_PIXELS = 1 << 20
@@ -79,7 +79,8 @@ class tsdf_tuning(ctypes.Structure):
                 ("fuse_mode", ctypes.c_int), ("probe_load", ctypes.c_int),
                 ("ctas_per_sm", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("candidates", ctypes.c_int), ("best_ms", ctypes.c_float),
-                ("default_ms", ctypes.c_float), ("threads_per_point", ctypes.c_int)]
+                ("default_ms", ctypes.c_float), ("threads_per_point", ctypes.c_int),
+                ("batch_streams", ctypes.c_int)]
 
 
 class tsdf_extract_timing(ctypes.Structure):

@@ -41,6 +41,7 @@ def check_tuning(t, batch):
     if batch:
         assert 0 <= t["ctas_per_sm"] <= 4 and t["use_graph"] in (0, 1)
         assert t["threads_per_point"] == 1
+        assert t["batch_streams"] in (0, 4, 8, 16)
     else:
         assert t["threads_per_point"] in (0, 1, 2, 4, 8)
         assert t["threads_per_point"] <= 1 or (t["fuse_mode"] == 2 and t["probe_load"] == 0)

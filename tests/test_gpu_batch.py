@@ -1,6 +1,9 @@
-"""Batched fusion (many sessions, one frame each per launch) against the
+"""Batched fusion (many sessions, one frame each per call) against the
 single-frame path and the CPU oracle: each session's result must be the same
-alone and in the mix (block-key set and weights exact, means within 1e-5)."""
+alone and in the mix (block-key set and weights exact, means within 1e-5).
+Both launch forms are covered: one launch per frame over the batch's streams
+(TSDF_OPT_BATCH_STREAMS k > 0, the default) and one persistent launch for the
+whole batch (0), with and without graphs."""
 import numpy as np
 import pytest
 
@@ -84,10 +87,20 @@ def run_single(ss, rounds):
     return vols
 
 
-@pytest.mark.parametrize("opts", [dict(), dict(fuse_mode=0), dict(fuse_mode=0, allocate_mode=2),
-                                  dict(fuse_mode=0, integrate_mode=1), dict(fuse_mode=1),
-                                  dict(use_graph=1), dict(use_graph=1, fuse_mode=0),
-                                  dict(use_graph=1, fuse_mode=1, ctas_per_sm=2)])
+PERSISTENT = dict(batch_streams=0)
+
+
+@pytest.mark.parametrize("opts", [
+    # one persistent launch for the whole batch
+    dict(PERSISTENT), dict(PERSISTENT, fuse_mode=0), dict(PERSISTENT, fuse_mode=0, allocate_mode=2),
+    dict(PERSISTENT, fuse_mode=0, integrate_mode=1), dict(PERSISTENT, fuse_mode=1),
+    dict(PERSISTENT, use_graph=1), dict(PERSISTENT, use_graph=1, fuse_mode=0),
+    dict(PERSISTENT, use_graph=1, fuse_mode=1, ctas_per_sm=2),
+    # one launch per frame over the batch's streams
+    dict(), dict(batch_streams=1), dict(batch_streams=3, fuse_mode=0),
+    dict(batch_streams=16, fuse_mode=1),
+    dict(batch_streams=5, fuse_mode=0, allocate_mode=2, integrate_mode=1),
+    dict(batch_streams=2, probe_load=1)])
 def test_batch_equals_single_frame_path(opts):
     ss = sessions(9)
     b = run_batched(ss, 2, **opts)
@@ -96,9 +109,10 @@ def test_batch_equals_single_frame_path(opts):
     assert total > 1000
 
 
-def test_batch_equals_oracle():
+@pytest.mark.parametrize("streams", [0, 8])
+def test_batch_equals_oracle(streams):
     ss = sessions(5, seed=11)
-    vols = run_batched(ss, 2, use_graph=1)
+    vols = run_batched(ss, 2, use_graph=1, batch_streams=streams)
     for s, v in zip(ss, vols):
         ov = oracle.OracleVolume(s["spec"].voxel_size, s["spec"].truncation,
                                  s["spec"].table_slots, s["spec"].pool_blocks)
@@ -111,11 +125,14 @@ def test_batch_equals_oracle():
         assert float(np.max(np.abs(gx[:, [0, 2, 3, 4]] - ox[:, [0, 2, 3, 4]]))) <= TOL
 
 
-def test_graph_replays_batches_of_changing_composition():
+@pytest.mark.parametrize("streams", [0, 4])
+def test_batches_of_changing_composition(streams):
+    """Graph replays (persistent launch) or lanes (per-frame launches) over
+    batches whose frames, sizes and count change from call to call."""
     ss = sessions(12, seed=5)
     vols = [new_volume(s["spec"]) for s in ss]
     ref = [new_volume(s["spec"]) for s in ss]
-    batch = tsdf.Batch(12, use_graph=1)
+    batch = tsdf.Batch(12, use_graph=1, batch_streams=streams)
     rng = np.random.default_rng(3)
     rounds = [0] * len(ss)
     for _ in range(5):
@@ -133,12 +150,13 @@ def test_graph_replays_batches_of_changing_composition():
         same(a, b)
 
 
-def test_batch_reports_overflow_per_frame():
+@pytest.mark.parametrize("streams", [0, 8])
+def test_batch_reports_overflow_per_frame(streams):
     ss = sessions(4, seed=9)
     vols = [new_volume(s["spec"]) for s in ss]
     tiny = tsdf.Volume(0.005, 0.02, 1 << 10, 8)
     vols[2] = tiny
-    batch = tsdf.Batch(4)
+    batch = tsdf.Batch(4, batch_streams=streams)
     items = []
     for s, v in zip(ss, vols):
         f = frame_of(s, 0)
@@ -163,17 +181,22 @@ def test_batch_rejects_bad_arguments():
     frames = tsdf.make_frames([(v.handle, d, c, f.intr, f.pose)] * 3)
     assert tsdf.tsdf_fuse_batch_async(batch.handle, frames, 3) == "INVALID_ARG"   # > max
     assert batch.set_option("allocate_mode", 0) == "INVALID_ARG"
+    assert batch.set_option("batch_streams", -1) == "INVALID_ARG"
+    assert batch.set_option("batch_streams", 17) == "INVALID_ARG"
+    assert batch.set_option("batch_streams", 16) == "OK"
 
 
-@pytest.mark.parametrize("use_graph", [0, 1])
-def test_batch_stages_one_at_a_time_equal_both(use_graph):
+@pytest.mark.parametrize("use_graph,streams", [(0, 0), (1, 0), (0, 8)])
+def test_batch_stages_one_at_a_time_equal_both(use_graph, streams):
     """TSDF_OPT_BATCH_STAGES: stage A of every frame in one call, then stage B
     of the same frames in another, equals the oracle (as both stages in one
     call do)."""
     ss = sessions(6, seed=13)
     vols = [new_volume(s["spec"]) for s in ss]
-    ba = tsdf.Batch(len(ss), fuse_mode=0, batch_stages=1, use_graph=use_graph)
-    bb = tsdf.Batch(len(ss), fuse_mode=0, batch_stages=2, use_graph=use_graph)
+    ba = tsdf.Batch(len(ss), fuse_mode=0, batch_stages=1, use_graph=use_graph,
+                    batch_streams=streams)
+    bb = tsdf.Batch(len(ss), fuse_mode=0, batch_stages=2, use_graph=use_graph,
+                    batch_streams=streams)
     for k in range(2):
         items = []
         for s, v in zip(ss, vols):
