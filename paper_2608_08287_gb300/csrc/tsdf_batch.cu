@@ -55,12 +55,14 @@ struct tsdf_batch {
   long long exec_key[2] = {-1, -1};
   // per-frame launches (TSDF_OPT_BATCH_STREAMS): lanes in use, lanes made,
   // the lanes and the event each records after its last launch, the fork
-  // event, and the launch order
+  // event
   int lanes = 0;
   int lanes_made = 0;
   cudaStream_t lane[16] = {};
   cudaEvent_t lane_done[16] = {};
   cudaEvent_t fork = nullptr;
+  // the caller's index of each entry of the last call's table (the table
+  // holds the frames largest first)
   int* order = nullptr;
 };
 
@@ -140,24 +142,17 @@ cudaError_t launch_one(const tsdf_batch* b, const tsdf::SessionArgs& a, int widt
   return e;
 }
 
-// Per-frame launches of the n frames whose arguments are in S, over the
-// batch's lanes, forked from and joined back into s.
-cudaError_t enqueue_lanes(tsdf_batch* b, const tsdf_frame* frames,
-                          const tsdf::SessionArgs* S, int n, cudaStream_t s) {
-  for (int i = 0; i < n; ++i) b->order[i] = i;
-  std::stable_sort(b->order, b->order + n, [frames](int x, int y) {
-    return static_cast<long long>(frames[x].width) * frames[x].height >
-           static_cast<long long>(frames[y].width) * frames[y].height;
-  });
+// Per-frame launches of the n frames whose arguments are in S (table order,
+// largest frames first), over the batch's lanes, forked from and joined back
+// into s.
+cudaError_t enqueue_lanes(tsdf_batch* b, const tsdf::SessionArgs* S, int n, cudaStream_t s) {
   const int lanes = std::min(b->lanes, n);
   cudaError_t e = cudaEventRecord(b->fork, s);
   for (int j = 0; j < lanes && e == cudaSuccess; ++j) e = cudaStreamWaitEvent(b->lane[j], b->fork, 0);
   if (e != cudaSuccess) return e;
-  for (int k = 0; k < n && e == cudaSuccess; ++k) {
-    const int i = b->order[k];
-    const tsdf_volume* v = frames[i].volume;
-    e = launch_one(b, S[i], frames[i].width, frames[i].height, v->half_band, v->sm_count,
-                   b->lane[k % lanes]);
+  for (int j = 0; j < n && e == cudaSuccess; ++j) {
+    const tsdf_volume* v = b->last_vols[j];
+    e = launch_one(b, S[j], S[j].f.W, S[j].f.H, v->half_band, v->sm_count, b->lane[j % lanes]);
   }
   // the join is enqueued even after a failed launch, so `s` stays ordered
   // after whatever the lanes did take
@@ -299,19 +294,28 @@ tsdf_status tsdf_fuse_batch_async(tsdf_batch* b, const tsdf_frame* frames, int n
   char* host = static_cast<char*>(b->table_host[slot]);
   tsdf::BatchHeader* hdr = reinterpret_cast<tsdf::BatchHeader*>(host);
   tsdf::SessionArgs* S = reinterpret_cast<tsdf::SessionArgs*>(hdr + 1);
+  // the table holds the frames largest first: the per-frame launches are
+  // issued in that order and the persistent kernels walk the tiles in it, so
+  // the big frames start first and the small ones fill in behind them.
+  // order[j] is the caller's index of table entry j.
+  for (int i = 0; i < n; ++i) b->order[i] = i;
+  std::stable_sort(b->order, b->order + n, [frames](int x, int y) {
+    return static_cast<long long>(frames[x].width) * frames[x].height >
+           static_cast<long long>(frames[y].width) * frames[y].height;
+  });
   int tiles = 0;
   bool all_m4 = true;
-  for (int i = 0; i < n; ++i) {
-    tsdf_volume* v = frames[i].volume;
-    tsdf::make_frame(v, frames[i].depth, frames[i].width, frames[i].height, &frames[i].intr,
-                     &frames[i].pose, frames[i].rgb, &S[i].f);
-    S[i].vol = v->va;
-    all_m4 = all_m4 && S[i].f.M == 4;
+  for (int j = 0; j < n; ++j) {
+    const tsdf_frame& fr = frames[b->order[j]];
+    tsdf_volume* v = fr.volume;
+    tsdf::make_frame(v, fr.depth, fr.width, fr.height, &fr.intr, &fr.pose, fr.rgb, &S[j].f);
+    S[j].vol = v->va;
+    all_m4 = all_m4 && S[j].f.M == 4;
     v->dirty = true;
-    S[i].tiles_x = (frames[i].width + 15) / 16;
-    S[i].tile_begin = tiles;
-    tiles += S[i].tiles_x * ((frames[i].height + 15) / 16);
-    b->last_vols[i] = v;
+    S[j].tiles_x = (fr.width + 15) / 16;
+    S[j].tile_begin = tiles;
+    tiles += S[j].tiles_x * ((fr.height + 15) / 16);
+    b->last_vols[j] = v;
   }
   hdr->n = n;
   hdr->total_tiles = tiles;
@@ -320,7 +324,7 @@ tsdf_status tsdf_fuse_batch_async(tsdf_batch* b, const tsdf_frame* frames, int n
   cudaStream_t s = as_stream(stream);
   cudaError_t e = cudaSuccess;
   if (b->lanes > 0) {
-    e = enqueue_lanes(b, frames, S, n, s);
+    e = enqueue_lanes(b, S, n, s);
     // the session table still goes to the device: tsdf_batch_status reads
     // each frame's volume header through it
     if (e == cudaSuccess)
@@ -379,12 +383,19 @@ tsdf_status tsdf_batch_status(tsdf_batch* b, void* stream, tsdf_status* per_fram
                         cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return from_cuda(e);
+  // table entry j is the caller's frame order[j]; the first error in the
+  // caller's order is returned
   tsdf_status worst = TSDF_OK;
-  for (int i = 0; i < b->last_n; ++i) {
-    const tsdf_status st = tsdf::decode_err(b->status_host[i]);
+  int worst_at = b->last_n;
+  for (int j = 0; j < b->last_n; ++j) {
+    const tsdf_status st = tsdf::decode_err(b->status_host[j]);
+    const int i = b->order[j];
     if (st != TSDF_OK) {
-      b->last_vols[i]->poisoned = true;
-      if (worst == TSDF_OK) worst = st;
+      b->last_vols[j]->poisoned = true;
+      if (i < worst_at) {
+        worst = st;
+        worst_at = i;
+      }
     }
     if (per_frame) per_frame[i] = st;
   }
