@@ -488,12 +488,14 @@ typedef struct tsdf_completion {
  * tsdf_fuse_batch_async, a launch of one frame the single-frame path); each
  * session's head frame is copied into staging as soon as a slot is free, on
  * a copy stream the server owns, and a launch waits only for its own frames'
- * copies. mode 1: one frame per launch with its copy just before it on
- * `stream` (the baseline). max_frame_pixels bounds a frame's size;
- * staging_frames (>= max_batch) device staging slots of that size are
- * allocated here (mode 0 also makes the copy stream and one event per slot),
- * and nothing is allocated afterwards. use_graph as TSDF_OPT_USE_GRAPH. The
- * fusion work is enqueued on `stream`. */
+ * copies; each launch in flight runs on one of max_inflight streams the
+ * server owns, after the work enqueued on `stream` before it, so that a
+ * launch runs beside those already in flight. mode 1: one frame per launch
+ * with its copy just before it, all on `stream` (the baseline).
+ * max_frame_pixels bounds a frame's size; staging_frames (>= max_batch)
+ * device staging slots of that size are allocated here (mode 0 also makes
+ * the copy stream, one event per slot and the launch streams), and nothing
+ * is allocated afterwards. use_graph as TSDF_OPT_USE_GRAPH. */
 tsdf_status tsdf_server_create(int mode, int max_batch, int max_inflight, int max_frame_pixels,
                                int staging_frames, int use_graph, void* stream,
                                tsdf_server** out);

@@ -12,11 +12,13 @@
 //      head of every session that has none in flight (oldest arrival first,
 //      at most max_batch) are launched -- as one batched fusion (mode 0; a
 //      batch of one frame takes the single-frame path, and the launch waits
-//      for the frames' copies), or one frame per launch with its copy just
-//      before it on the same stream (mode 1, the baseline).
-// Each session's frames therefore run in arrival order (one stream, at most
-// one frame of a session per launch), frames that arrive while others run join
-// the next launch, and nothing is allocated after creation.
+//      for the frames' copies) on a stream of its own, so that it runs beside
+//      the launches already in flight, or one frame per launch with its copy
+//      just before it, all on the caller's stream (mode 1, the baseline).
+// Each session's frames therefore run in arrival order (at most one frame of
+// a session in flight, and the next launched only after it retired), frames
+// that arrive while others run join the next launch, and nothing is allocated
+// after creation.
 #include <algorithm>
 #include <chrono>
 #include <cstring>
@@ -49,6 +51,7 @@ struct InFlight {
   cudaEvent_t ev;
   std::vector<Pending> frames;
   std::vector<int> slots;
+  int lane = -1;  // mode 0: the stream it runs on
 };
 
 }  // namespace
@@ -64,6 +67,9 @@ struct tsdf_server {
   cudaStream_t stream = nullptr;
   cudaStream_t copy_stream = nullptr;      // mode 0: the eager copies
   std::vector<cudaEvent_t> slot_copied;    // mode 0: per staging slot, its copy done
+  std::vector<cudaStream_t> lanes;         // mode 0: one stream per launch in flight
+  std::vector<int> free_lanes;
+  cudaEvent_t caller_ev = nullptr;         // mode 0: the caller's stream, before a launch
   std::unordered_map<tsdf_volume*, std::deque<Pending>> queues;
   std::unordered_map<tsdf_volume*, int> busy;
   std::deque<InFlight> inflight;
@@ -134,6 +140,7 @@ bool launch_some(tsdf_server* s) {
                                }),
                 ready.end());
     if (ready.empty()) return false;
+    if (s->free_lanes.empty()) return false;
   } else if (s->free_slots.empty()) {
     return false;
   }
@@ -142,6 +149,15 @@ bool launch_some(tsdf_server* s) {
   if (s->mode == 1 && take > static_cast<int>(s->free_slots.size()))
     take = static_cast<int>(s->free_slots.size());
   InFlight f;
+  cudaStream_t ls = s->stream;
+  if (s->mode == 0) {
+    // a stream of its own, ordered after the caller's stream
+    f.lane = s->free_lanes.back();
+    s->free_lanes.pop_back();
+    ls = s->lanes[f.lane];
+    note_cuda(s, cudaEventRecord(s->caller_ev, s->stream));
+    note_cuda(s, cudaStreamWaitEvent(ls, s->caller_ev, 0));
+  }
   std::vector<tsdf_frame> frames;
   frames.reserve(take);
   for (int i = 0; i < take; ++i) {
@@ -154,16 +170,16 @@ bool launch_some(tsdf_server* s) {
       s->free_slots.pop_back();
     }
     if (p.reset) {
-      const tsdf_status rs = tsdf_volume_reset(v, s->stream);
+      const tsdf_status rs = tsdf_volume_reset(v, ls);
       if (rs != TSDF_OK && s->sticky == TSDF_OK) s->sticky = rs;
     }
     char* dst = s->staging + static_cast<size_t>(slot) * s->slot_bytes;
     const size_t npx = static_cast<size_t>(p.w) * p.h;
     const size_t dbytes = tsdf::align_up(npx * sizeof(float));
     if (p.slot < 0)
-      copy_in(s, p, slot, s->stream);
+      copy_in(s, p, slot, ls);
     else
-      note_cuda(s, cudaStreamWaitEvent(s->stream, s->slot_copied[slot], 0));
+      note_cuda(s, cudaStreamWaitEvent(ls, s->slot_copied[slot], 0));
     tsdf_frame fr;
     fr.volume = v;
     fr.depth = reinterpret_cast<const float*>(dst);
@@ -181,15 +197,14 @@ bool launch_some(tsdf_server* s) {
   if (frames.size() == 1) {
     const tsdf_frame& fr = frames[0];
     st = tsdf_fuse_frame_async(fr.volume, fr.depth, fr.width, fr.height, &fr.intr, &fr.pose,
-                               fr.rgb, s->stream);
+                               fr.rgb, ls);
   } else {
-    st = tsdf_fuse_batch_async(s->batch, frames.data(), static_cast<int>(frames.size()),
-                               s->stream);
+    st = tsdf_fuse_batch_async(s->batch, frames.data(), static_cast<int>(frames.size()), ls);
   }
   if (st != TSDF_OK && s->sticky == TSDF_OK) s->sticky = st;
   f.ev = s->events.back();
   s->events.pop_back();
-  note_cuda(s, cudaEventRecord(f.ev, s->stream));
+  note_cuda(s, cudaEventRecord(f.ev, ls));
   s->inflight.push_back(std::move(f));
   return true;
 }
@@ -208,6 +223,7 @@ void retire(tsdf_server* s) {
       s->free_slots.push_back(f.slots[i]);
       --s->pending;
     }
+    if (f.lane >= 0) s->free_lanes.push_back(f.lane);
     s->events.push_back(f.ev);
     s->inflight.pop_front();
   }
@@ -264,6 +280,20 @@ tsdf_status tsdf_server_create(int mode, int max_batch, int max_inflight, int ma
         return TSDF_ERR_CUDA;
       }
     }
+    if (cudaEventCreateWithFlags(&s->caller_ev, cudaEventDisableTiming) != cudaSuccess) {
+      s->caller_ev = nullptr;
+      tsdf_server_destroy(s);
+      return TSDF_ERR_CUDA;
+    }
+    for (int i = 0; i < max_inflight; ++i) {
+      cudaStream_t ls = nullptr;
+      if (cudaStreamCreateWithFlags(&ls, cudaStreamNonBlocking) != cudaSuccess) {
+        tsdf_server_destroy(s);
+        return TSDF_ERR_CUDA;
+      }
+      s->lanes.push_back(ls);
+      s->free_lanes.push_back(max_inflight - 1 - i);
+    }
   }
   tsdf_status st = TSDF_OK;
   if (mode == 0) {
@@ -281,6 +311,11 @@ tsdf_status tsdf_server_create(int mode, int max_batch, int max_inflight, int ma
 void tsdf_server_destroy(tsdf_server* s) {
   if (!s) return;
   cudaStreamSynchronize(s->stream);
+  for (cudaStream_t ls : s->lanes) {
+    cudaStreamSynchronize(ls);
+    cudaStreamDestroy(ls);
+  }
+  if (s->caller_ev) cudaEventDestroy(s->caller_ev);
   for (auto& f : s->inflight) s->events.push_back(f.ev);
   for (cudaEvent_t ev : s->events) cudaEventDestroy(ev);
   if (s->copy_stream) cudaStreamSynchronize(s->copy_stream);
