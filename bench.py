@@ -787,13 +787,15 @@ def run_serving(args, torch, serving, bank):
            "frames_offered": int(sum(len(p.arrivals) for p in admitted))}
     out["server"] = "tsdf_server (native continuous batching) vs one launch per frame"
     out["repeats"] = args.serve_repeats
+    out["max_inflight"] = args.serve_inflight
     for speed in [1.0] + [float(x) for x in str(args.serve_stress).split(",") if x]:
         into = out if speed == 1.0 else out.setdefault(f"stress_{speed:g}x", {})
         runs = {"batched": [], "per_frame": []}
         for rep in range(args.serve_repeats):
             # the two servers alternate, so drifts of the box hit both alike
             for name, mode in (("batched", 0), ("per_frame", 1)):
-                res, st, _ = serving.native_replay(torch, bank, plans, mode, speed=speed)
+                res, st, _ = serving.native_replay(torch, bank, plans, mode, speed=speed,
+                                                   max_inflight=args.serve_inflight)
                 torch.cuda.synchronize()
                 summ = res.summary()
                 summ["status"] = st
@@ -1338,6 +1340,8 @@ def main():
     ap.add_argument("--serve-window", type=float, default=10.0)
     ap.add_argument("--serve-repeats", type=int, default=3,
                     help="runs of each server at each arrival rate (median reported, spread kept)")
+    ap.add_argument("--serve-inflight", type=int, default=4,
+                    help="launches in flight at most, for both servers")
     ap.add_argument("--serve-stress", default="3,10",
                     help="arrival-rate multiples of the further serving runs (comma-separated)")
     ap.add_argument("--bank-frames", type=int, default=24)

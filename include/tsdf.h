@@ -372,8 +372,9 @@ tsdf_status tsdf_fuse_batch_async(tsdf_batch* batch, const tsdf_frame* frames, i
                                   void* stream);
 
 /* Wait for `stream` and report the status of every frame of the last batch
- * (per_frame may be NULL; otherwise n >= that batch's size). Returns the first
- * error found, and poisons the volumes that have one. */
+ * (per_frame may be NULL; otherwise n >= that batch's size; per_frame[i] is
+ * frames[i]'s). Returns the error of the first frame, in the call's order,
+ * that has one, and poisons the volumes that have one. */
 tsdf_status tsdf_batch_status(tsdf_batch* batch, void* stream, tsdf_status* per_frame, int n);
 
 /* ---------------------------------------------------------------------------

@@ -389,10 +389,11 @@ def assign_volumes(plans):
 
 
 def native_replay(torch, bank, plans, mode, max_batch=128, use_graph=True, speed=1.0,
-                  reuse_volumes=True, keep_volumes=False):
+                  reuse_volumes=True, keep_volumes=False, max_inflight=4):
     """Replay the schedule through tsdf_server (mode 0: continuous batching,
-    mode 1: one frame per launch). Returns (Result, status, volumes by sid or
-    None). Frames come from the bank's pinned host buffers."""
+    mode 1: one frame per launch), at most max_inflight launches in flight.
+    Returns (Result, status, volumes by sid or None). Frames come from the
+    bank's pinned host buffers."""
     plans = [p for p in plans if len(p.arrivals)]
     if reuse_volumes:
         where, counts = assign_volumes(plans)
@@ -427,8 +428,8 @@ def native_replay(torch, bank, plans, mode, max_batch=128, use_graph=True, speed
         points += pts
     stream = torch.cuda.Stream()
     max_px = max(w * h for w, h in bank.res)
-    server = tsdf.tsdf_server_create(mode, max_batch, 2, max_px, 2 * max_batch + 8,
-                                     use_graph, stream.cuda_stream)
+    server = tsdf.tsdf_server_create(mode, max_batch, max_inflight, max_px,
+                                     max_inflight * max_batch + 8, use_graph, stream.cuda_stream)
     try:
         st, comp = tsdf.tsdf_server_replay(server, reqs)
     finally:
