@@ -32,6 +32,11 @@
 using tsdf::as_stream;
 using tsdf::from_cuda;
 
+namespace {
+constexpr int kMaxLanes = 16;     // streams a batch can own
+constexpr int kDefaultLanes = 8;  // TSDF_OPT_BATCH_STREAMS at creation
+}  // namespace
+
 struct tsdf_batch {
   int device = 0;
   int max_frames = 0;
@@ -58,8 +63,8 @@ struct tsdf_batch {
   // event
   int lanes = 0;
   int lanes_made = 0;
-  cudaStream_t lane[16] = {};
-  cudaEvent_t lane_done[16] = {};
+  cudaStream_t lane[kMaxLanes] = {};
+  cudaEvent_t lane_done[kMaxLanes] = {};
   cudaEvent_t fork = nullptr;
   // the caller's index of each entry of the last call's table (the table
   // holds the frames largest first)
@@ -95,9 +100,6 @@ cudaError_t enqueue(tsdf_batch* b, int slot, size_t bytes, int grid_limit, bool 
 // A batch smaller than this many tiles is launched directly with a grid of its
 // own size: a replayed graph's persistent grid would mostly idle.
 constexpr int kGraphMinTiles = 2048;
-
-constexpr int kMaxLanes = 16;
-constexpr int kDefaultLanes = 8;
 
 // Make lanes up to k (streams that do not synchronise with the legacy default
 // stream, and their events).
