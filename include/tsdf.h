@@ -155,13 +155,14 @@ typedef enum tsdf_option {
    * floating-point additions. Safe without a grid barrier because a point
    * only touches blocks whose indices it has resolved. */
   TSDF_OPT_FUSE_MODE = 5,
-  /* Batches only: cap on resident CTAs per SM of the persistent batched
-   * kernels (0 = as many as fit, default). */
+  /* Batches only, with TSDF_OPT_BATCH_STREAMS 0: cap on resident CTAs per SM
+   * of the persistent batched kernels (0 = as many as fit, default). */
   TSDF_OPT_CTAS_PER_SM = 6,
-  /* Batches only: 1 = capture each configuration's copy-and-launch sequence
-   * in a CUDA graph once and replay it for batches of at least 2048 tiles;
-   * smaller batches are launched directly with a grid of their own size
-   * (default 0: always launch directly). */
+  /* Batches only, with TSDF_OPT_BATCH_STREAMS 0: 1 = capture each
+   * configuration's copy-and-launch sequence in a CUDA graph once and replay
+   * it for batches of at least 2048 tiles; smaller batches are launched
+   * directly with a grid of their own size (default 0: always launch
+   * directly). */
   TSDF_OPT_USE_GRAPH = 7,
   /* 1 = a block's pool index is its table slot (Section 6, "Deriving the
    * location from the slot"): the slot winner only counts the block, a thread
