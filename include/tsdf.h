@@ -204,7 +204,8 @@ typedef enum tsdf_option {
    * stage (the batched kernels; TSDF_OPT_CTAS_PER_SM and TSDF_OPT_USE_GRAPH
    * apply); k = 1..16 = every frame in a launch of its own -- the
    * single-frame kernels, with the batch's strategy options and the threads
-   * per point chosen per frame as for a volume set to 0 -- the frames taken
+   * per point that the automatic choice of a volume would give one frame of
+   * all the call's tiles (1 when they fill the GPU) -- the frames taken
    * largest first and dealt round-robin over k streams the batch owns, which
    * wait for `stream` before their first launch and which `stream` waits for
    * after their last (concurrent kernels fill the GPU where one small frame

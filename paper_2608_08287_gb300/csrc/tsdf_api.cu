@@ -182,12 +182,11 @@ tsdf_status make_frame(const tsdf_volume* v, const float* depth, int w, int h,
   return TSDF_OK;
 }
 
-int auto_threads_per_point(int fuse_mode, int probe_load, int half_band, int sm_count, int width,
-                           int height) {
+int auto_threads_per_point(int fuse_mode, int probe_load, int half_band, int sm_count,
+                           long long tiles) {
   if (fuse_mode != 2 || probe_load != kLoadCached ||
       (half_band != 2 && half_band != 4 && half_band != 8))
     return 1;
-  const long long tiles = static_cast<long long>((width + 15) / 16) * ((height + 15) / 16);
   const long long slots = 4ll * (sm_count > 0 ? sm_count : 1);
   int t = 1;
   while (t < 4 && tiles * (2 * t) <= slots) t *= 2;
@@ -206,7 +205,7 @@ int threads_per_point(const tsdf_volume* vol, int width, int height) {
   if (vol->fuse_mode != 2) return 1;
   if (vol->threads_per_point != 0) return vol->threads_per_point;
   return tsdf::auto_threads_per_point(vol->fuse_mode, vol->probe_load, vol->half_band,
-                                      vol->sm_count, width, height);
+                                      vol->sm_count, tsdf::tiles_of_frame(width, height));
 }
 
 // Host-side header of a checkpoint, followed by the volume's whole device

@@ -8,7 +8,8 @@
 // the small ones fill the GPU around them; each stream waits for an event on
 // the caller's stream before its first launch, and the caller's stream waits
 // for each stream's last. Each frame runs the single-frame kernels with its
-// arguments in the kernel's parameter space.
+// arguments in the kernel's parameter space, with the threads per point the
+// whole call's tile count gives (one when the batch fills the GPU).
 //
 // A batch owns two session tables (double buffering): a pinned host copy the
 // caller's frames are written into, and a device copy the kernels read. Each
@@ -130,12 +131,15 @@ cudaError_t make_lanes(tsdf_batch* b, int k) {
   return cudaSuccess;
 }
 
-// Launch one frame's fusion with the batch's strategy on stream s.
-cudaError_t launch_one(const tsdf_batch* b, const tsdf::SessionArgs& a, int width, int height,
+// Launch one frame's fusion with the batch's strategy on stream s; its
+// threads per point are chosen for all `batch_tiles` tiles of the call, which
+// run together (a frame that would be split alone is not when the batch fills
+// the GPU: there the split only adds work).
+cudaError_t launch_one(const tsdf_batch* b, const tsdf::SessionArgs& a, long long batch_tiles,
                        int half_band, int sm_count, cudaStream_t s) {
   if (b->fuse_mode != 0) {
     const int tpp = tsdf::auto_threads_per_point(b->fuse_mode, b->probe_load, half_band,
-                                                 sm_count, width, height);
+                                                 sm_count, batch_tiles);
     return tsdf::launch_fused(a.f, a.vol, b->probe_load, b->fuse_mode, tpp, s);
   }
   cudaError_t e = cudaSuccess;
@@ -147,14 +151,15 @@ cudaError_t launch_one(const tsdf_batch* b, const tsdf::SessionArgs& a, int widt
 // Per-frame launches of the n frames whose arguments are in S (table order,
 // largest frames first), over the batch's lanes, forked from and joined back
 // into s.
-cudaError_t enqueue_lanes(tsdf_batch* b, const tsdf::SessionArgs* S, int n, cudaStream_t s) {
+cudaError_t enqueue_lanes(tsdf_batch* b, const tsdf::SessionArgs* S, int n, long long tiles,
+                          cudaStream_t s) {
   const int lanes = std::min(b->lanes, n);
   cudaError_t e = cudaEventRecord(b->fork, s);
   for (int j = 0; j < lanes && e == cudaSuccess; ++j) e = cudaStreamWaitEvent(b->lane[j], b->fork, 0);
   if (e != cudaSuccess) return e;
   for (int j = 0; j < n && e == cudaSuccess; ++j) {
     const tsdf_volume* v = b->last_vols[j];
-    e = launch_one(b, S[j], S[j].f.W, S[j].f.H, v->half_band, v->sm_count, b->lane[j % lanes]);
+    e = launch_one(b, S[j], tiles, v->half_band, v->sm_count, b->lane[j % lanes]);
   }
   // the join is enqueued even after a failed launch, so `s` stays ordered
   // after whatever the lanes did take
@@ -326,7 +331,7 @@ tsdf_status tsdf_fuse_batch_async(tsdf_batch* b, const tsdf_frame* frames, int n
   cudaStream_t s = as_stream(stream);
   cudaError_t e = cudaSuccess;
   if (b->lanes > 0) {
-    e = enqueue_lanes(b, S, n, s);
+    e = enqueue_lanes(b, S, n, tiles, s);
     // the session table still goes to the device: tsdf_batch_status reads
     // each frame's volume header through it
     if (e == cudaSuccess)

@@ -25,13 +25,17 @@ inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s
 tsdf_status from_cuda(cudaError_t e);
 tsdf_status decode_err(uint32_t err);
 
-// Threads per point of the fused tile kernel chosen for a width x height
-// frame: the largest of 1, 2, 4 whose CTAs (one per 16 x 16/TPP pixel tile)
-// still fit the GPU's resident slots at four CTAs per SM -- a frame that fills
+// Threads per point of the fused tile kernel chosen for work of `tiles`
+// 16 x 16 pixel tiles running alone on the GPU (one frame, or all frames of a
+// batch launched together): the largest of 1, 2, 4 whose CTAs (tiles x TPP)
+// still fit the GPU's resident slots at four CTAs per SM -- work that fills
 // the GPU keeps one thread per point -- where the split walk exists (fuse
 // mode 2, the default probe load, half band 2, 4 or 8), else 1.
-int auto_threads_per_point(int fuse_mode, int probe_load, int half_band, int sm_count, int width,
-                           int height);
+int auto_threads_per_point(int fuse_mode, int probe_load, int half_band, int sm_count,
+                           long long tiles);
+inline long long tiles_of_frame(int width, int height) {
+  return static_cast<long long>((width + 15) / 16) * ((height + 15) / 16);
+}
 
 }  // namespace tsdf
 
