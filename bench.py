@@ -36,6 +36,29 @@ METRIC = ("depth pts fused/s (alloc+integrate, 640x480) + % HBM roofline; "
           "serving p50/p99")
 UNIT = "pts/s"
 WORKLOAD = "room_640x480_single_frame"
+
+# The paper's own full integrate path (allocate plus update), median of three
+# passes, on the two sm_120 GPUs it names (Section 5, the table of full
+# integrate times; synthetic rows only: the real-depth rows need a dataset
+# that is not here). Other hardware and other scenes: context, not a target.
+PAPER_CONTEXT = {
+    "source": "Section 5, full integrate path (allocate + update), median of three passes",
+    "rows": [
+        {"workload": "plane, 320,356 points", "gpu": "RTX 5070 Ti",
+         "ms": {"cuda_cpp": 0.363, "rust": 0.379, "triton": 0.875}},
+        {"workload": "plane, 320,356 points", "gpu": "RTX 5060",
+         "ms": {"cuda_cpp": 0.673, "rust": 0.686, "triton": 1.665}},
+        {"workload": "sphere, 320k points", "gpu": "RTX 5070 Ti",
+         "ms": {"cuda_cpp": 0.278, "rust": 0.308, "triton": 0.828}},
+        {"workload": "sphere, 320k points", "gpu": "RTX 5060",
+         "ms": {"cuda_cpp": 0.511, "rust": 0.538, "triton": 1.526}},
+        {"workload": "sphere, 1.28M points", "gpu": "RTX 5070 Ti",
+         "ms": {"cuda_cpp": 0.975, "rust": 1.023, "triton": 2.982}},
+        {"workload": "sphere, 1.28M points", "gpu": "RTX 5060",
+         "ms": {"cuda_cpp": 1.709, "rust": 1.737, "triton": 5.707}},
+    ],
+    "best_pts_per_s": {"value": 1.31e9, "row": "sphere, 1.28M points, CUDA C++, RTX 5070 Ti"},
+}
 N_FRAMES = 4           # distinct orbit frames, cycled over the steps
 FLUSH_BYTES = 512 << 20
 
@@ -425,6 +448,7 @@ def run_gpu(args, rank, world, local_rank):
             "clocks": clk.summary(),
             "wall_s_timed_region": round(wall, 4),
             "kernel_source": kernel_source_hash(),
+            "paper_context": PAPER_CONTEXT,
         }
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
