@@ -812,7 +812,16 @@ def run_serving(args, torch, serving, bank):
     out["server"] = "tsdf_server (native continuous batching) vs one launch per frame"
     out["repeats"] = args.serve_repeats
     out["max_inflight"] = args.serve_inflight
-    for speed in [1.0] + [float(x) for x in str(args.serve_stress).split(",") if x]:
+    speeds = [1.0] + [float(x) for x in str(args.serve_stress).split(",") if x]
+    # warm-up, not recorded: the whole schedule once at the highest rate for
+    # each server, so every kernel the servers launch is loaded (lazily, on
+    # first use) before the measured runs
+    for mode in (0, 1):
+        serving.native_replay(torch, bank, plans, mode, speed=max(speeds),
+                              max_inflight=args.serve_inflight)
+        torch.cuda.synchronize()
+    out["warmup"] = f"one unrecorded replay per server at {max(speeds):g}x"
+    for speed in speeds:
         into = out if speed == 1.0 else out.setdefault(f"stress_{speed:g}x", {})
         runs = {"batched": [], "per_frame": []}
         for rep in range(args.serve_repeats):
@@ -1362,7 +1371,7 @@ def main():
                     help="nvidia-smi sampling interval during the timed region")
     ap.add_argument("--serve-sessions", type=int, default=256)
     ap.add_argument("--serve-window", type=float, default=10.0)
-    ap.add_argument("--serve-repeats", type=int, default=3,
+    ap.add_argument("--serve-repeats", type=int, default=5,
                     help="runs of each server at each arrival rate (median reported, spread kept)")
     ap.add_argument("--serve-inflight", type=int, default=4,
                     help="launches in flight at most, for both servers")

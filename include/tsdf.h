@@ -488,7 +488,8 @@ typedef struct tsdf_completion {
 } tsdf_completion;
 
 /* mode 0: continuous batching (a launch of several frames uses
- * tsdf_fuse_batch_async, a launch of one frame the single-frame path); each
+ * tsdf_fuse_batch_async, with a batch context for each launch stream; a
+ * launch of one frame takes the single-frame path); each
  * session's head frame is copied into staging as soon as a slot is free, on
  * a copy stream the server owns, and a launch waits only for its own frames'
  * copies; each launch in flight runs on one of max_inflight streams the
@@ -497,7 +498,8 @@ typedef struct tsdf_completion {
  * with its copy just before it, all on `stream` (the baseline).
  * max_frame_pixels bounds a frame's size; staging_frames (>= max_batch)
  * device staging slots of that size are allocated here (mode 0 also makes
- * the copy stream, one event per slot and the launch streams), and nothing
+ * the copy stream, one event per slot, the launch streams and their batch
+ * contexts), and nothing
  * is allocated afterwards. use_graph as TSDF_OPT_USE_GRAPH. */
 tsdf_status tsdf_server_create(int mode, int max_batch, int max_inflight, int max_frame_pixels,
                                int staging_frames, int use_graph, void* stream,

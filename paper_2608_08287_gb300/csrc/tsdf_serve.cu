@@ -63,7 +63,9 @@ struct tsdf_server {
   int max_pixels = 0;
   char* staging = nullptr;
   std::vector<int> free_slots;
-  tsdf_batch* batch = nullptr;
+  // mode 0: one batch context per launch stream, so launches in flight never
+  // share a batch's session tables or its streams
+  std::vector<tsdf_batch*> batches;
   cudaStream_t stream = nullptr;
   cudaStream_t copy_stream = nullptr;      // mode 0: the eager copies
   std::vector<cudaEvent_t> slot_copied;    // mode 0: per staging slot, its copy done
@@ -199,7 +201,8 @@ bool launch_some(tsdf_server* s) {
     st = tsdf_fuse_frame_async(fr.volume, fr.depth, fr.width, fr.height, &fr.intr, &fr.pose,
                                fr.rgb, ls);
   } else {
-    st = tsdf_fuse_batch_async(s->batch, frames.data(), static_cast<int>(frames.size()), ls);
+    st = tsdf_fuse_batch_async(s->batches[f.lane], frames.data(), static_cast<int>(frames.size()),
+                               ls);
   }
   if (st != TSDF_OK && s->sticky == TSDF_OK) s->sticky = st;
   f.ev = s->events.back();
@@ -297,8 +300,12 @@ tsdf_status tsdf_server_create(int mode, int max_batch, int max_inflight, int ma
   }
   tsdf_status st = TSDF_OK;
   if (mode == 0) {
-    st = tsdf_batch_create(max_batch, &s->batch);
-    if (st == TSDF_OK && use_graph) st = tsdf_batch_set_option(s->batch, TSDF_OPT_USE_GRAPH, 1);
+    for (int i = 0; i < max_inflight && st == TSDF_OK; ++i) {
+      tsdf_batch* bt = nullptr;
+      st = tsdf_batch_create(max_batch, &bt);
+      if (st == TSDF_OK) s->batches.push_back(bt);
+      if (st == TSDF_OK && use_graph) st = tsdf_batch_set_option(bt, TSDF_OPT_USE_GRAPH, 1);
+    }
   }
   if (st != TSDF_OK) {
     tsdf_server_destroy(s);
@@ -322,7 +329,7 @@ void tsdf_server_destroy(tsdf_server* s) {
   for (cudaEvent_t ev : s->slot_copied)
     if (ev) cudaEventDestroy(ev);
   if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
-  if (s->batch) tsdf_batch_destroy(s->batch);
+  for (tsdf_batch* bt : s->batches) tsdf_batch_destroy(bt);
   if (s->staging) cudaFree(s->staging);
   delete s;
 }
