@@ -1054,7 +1054,9 @@ def run_batch_profile_case(args):
             for sp, _ in sess]
     dev = [(torch.from_numpy(f.depth).cuda(), torch.from_numpy(f.rgb).cuda()) for _, f in sess]
     items = [(v, d, c, f.intr, f.pose) for v, (d, c), (_, f) in zip(vols, dev, sess)]
-    batch = tsdf.Batch(len(sess), use_graph=1, batch_streams=0)   # the persistent form
+    # the persistent form by default; --batch-case-streams k > 0 takes the
+    # per-frame form over k streams
+    batch = tsdf.Batch(len(sess), use_graph=1, batch_streams=args.batch_case_streams)
     reps = args.batch_case_reps
     flush = scrub = None
     if reps > 0:
@@ -1083,8 +1085,10 @@ def run_batch_profile_case(args):
         v.close()
     ms = float(np.median(times))
     hbm, peak_kind = peaks()
-    return {"case": "batch_tile_fused_kernel, 16 sessions (8 x 320x240, 8 x 160x120 room "
-                    "frames), each into an empty volume",
+    return {"case": ("batch_tile_fused_kernel" if args.batch_case_streams == 0 else
+                     f"tile_fused_kernel per frame over {args.batch_case_streams} streams") +
+                    ", 16 sessions (8 x 320x240, 8 x 160x120 room frames), each into an "
+                    "empty volume",
             "tiles": sum(((w + 15) // 16) * ((h + 15) // 16) for w, h in
                          (classes[i % 2] for i in range(BATCH_CASE_SESSIONS))),
             "points": int(points), "reps": reps, "ms_median": round(ms, 4),
@@ -1394,6 +1398,9 @@ def main():
     ap.add_argument("--batch-profile-case", action="store_true",
                     help="only the batched fused kernel on a 16-session case of about 1.5 GB "
                          "(a small command for an ncu capture of the batched kernel)")
+    ap.add_argument("--batch-case-streams", type=int, default=0,
+                    help="batch profile case: 0 = the persistent batched kernel, k > 0 = one "
+                         "launch per frame over k streams")
     ap.add_argument("--batch-case-reps", type=int, default=20,
                     help="timed batches of the batch profile case (0: one batch after a "
                          "warm-up, no L2 scrub, for an ncu capture)")
