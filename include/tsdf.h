@@ -350,8 +350,9 @@ typedef struct tsdf_frame {
 } tsdf_frame;
 
 /* A batch context for up to max_frames frames per call, on the current
- * device: two session tables (device + pinned host, double-buffered) and a
- * status buffer. */
+ * device: two session tables (device + pinned host, double-buffered), a
+ * status buffer, and the streams of TSDF_OPT_BATCH_STREAMS (8 at creation).
+ * One host thread at a time may call into a batch context. */
 tsdf_status tsdf_batch_create(int max_frames, tsdf_batch** out);
 void tsdf_batch_destroy(tsdf_batch* batch);
 
