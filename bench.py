@@ -716,29 +716,35 @@ def run_batched(args, torch, tsdf, serving, bank):
         assert v.status(sp_) == "OK"
 
     # the two-stage batched path, each stage timed on its own: stage A (tile
-    # allocator) as one persistent launch over the 64 frames, then stage B
-    # (per-thread scatter) as another, each replayed from its own graph
-    batch_a = tsdf.Batch(n, use_graph=1, fuse_mode=0, allocate_mode=1, integrate_mode=0,
-                         batch_stages=1, batch_streams=0)
-    batch_b = tsdf.Batch(n, use_graph=1, fuse_mode=0, allocate_mode=1, integrate_mode=0,
-                         batch_stages=2, batch_streams=0)
-    ta_, tb_ = [], []
-    for i in range(3 + args.batch_steps):
-        prep(i)
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-        ev[0].record(stream)
-        assert batch_a.fuse_async(items, stream=sp_) == "OK"
-        ev[1].record(stream)
-        assert batch_b.fuse_async(items, stream=sp_) == "OK"
-        ev[2].record(stream)
-        stream.synchronize()
-        if i >= 3:
-            ta_.append(ev[0].elapsed_time(ev[1]))
-            tb_.append(ev[1].elapsed_time(ev[2]))
-    st, _ = batch_b.status(n, stream=sp_)
-    assert st == "OK", st
-    batch_a.close()
-    batch_b.close()
+    # allocator) for all 64 frames, then stage B (per-thread scatter), in the
+    # persistent form (one launch each, replayed from its own graph) and in
+    # the per-frame form (one launch per frame and stage over 8 streams)
+    def stage_times(streams):
+        batch_a = tsdf.Batch(n, use_graph=1, fuse_mode=0, allocate_mode=1, integrate_mode=0,
+                             batch_stages=1, batch_streams=streams)
+        batch_b = tsdf.Batch(n, use_graph=1, fuse_mode=0, allocate_mode=1, integrate_mode=0,
+                             batch_stages=2, batch_streams=streams)
+        ta, tb2 = [], []
+        for i in range(3 + args.batch_steps):
+            prep(i)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            ev[0].record(stream)
+            assert batch_a.fuse_async(items, stream=sp_) == "OK"
+            ev[1].record(stream)
+            assert batch_b.fuse_async(items, stream=sp_) == "OK"
+            ev[2].record(stream)
+            stream.synchronize()
+            if i >= 3:
+                ta.append(ev[0].elapsed_time(ev[1]))
+                tb2.append(ev[1].elapsed_time(ev[2]))
+        st_, _ = batch_b.status(n, stream=sp_)
+        assert st_ == "OK", st_
+        batch_a.close()
+        batch_b.close()
+        return ta, tb2
+
+    ta_, tb_ = stage_times(0)
+    ta_l, tb_l = stage_times(8)
     # algorithmic bytes of the batch from the oracle's work counts of its frames
     wk = oracle_work_counts([(d.numpy(), c.numpy(), np.array([intr.fx, intr.fy, intr.cx, intr.cy],
                                                               np.float32),
@@ -759,6 +765,17 @@ def run_batched(args, torch, tsdf, serving, bank):
                     "algorithmic_bytes": int(sums[1]),
                     "frac": round(sums[1] / (sb_ms * 1e6) / hbm, 4)},
         "two_stage_pts_per_s": round(points / ((sa_ms + sb_ms) / 1e3), 1),
+        "two_stage_per_frame_pts_per_s": round(
+            points / ((float(np.mean(ta_l)) + float(np.mean(tb_l))) / 1e3), 1),
+        "stage_a_per_frame": {"kernel": "tile_allocate_kernel, one launch per frame over 8 streams",
+                              "ms": round(float(np.mean(ta_l)), 4),
+                              "algorithmic_bytes": int(sums[0]),
+                              "frac": round(sums[0] / (float(np.mean(ta_l)) * 1e6) / hbm, 4)},
+        "stage_b_per_frame": {"kernel": "integrate_scatter_kernel, one launch per frame over 8 "
+                                        "streams",
+                              "ms": round(float(np.mean(tb_l)), 4),
+                              "algorithmic_bytes": int(sums[1]),
+                              "frac": round(sums[1] / (float(np.mean(tb_l)) * 1e6) / hbm, 4)},
         "fused": {"kernel": "tile_fused_kernel, one launch per frame over 8 streams (default)",
                   "ms": round(float(np.mean(tb)), 4), "algorithmic_bytes": int(sums[2]),
                   "frac": round(sums[2] / (float(np.mean(tb)) * 1e6) / hbm, 4)},
